@@ -1,0 +1,189 @@
+/*
+ * pll.h -- C ABI of libpll.so: GB300 (sm_103a) index construction and
+ * distance queries for Pruned Landmark Labeling (Akiba, Iwata, Yoshida,
+ * "Fast Exact Shortest-Path Distance Queries on Large Networks by Pruned
+ * Landmark Labeling", SIGMOD 2013).
+ *
+ * Problem (Sec. 3.2): given an undirected, unweighted graph G = (V, E), build
+ * an index that answers the distance d_G(s, t) for any pair exactly.
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are symmetric CSR: offsets[n + 1] (uint32, offsets[0] = 0,
+ *     non-decreasing, offsets[n] = nnz) and cols[nnz] (uint32 vertex ids).
+ *     Every undirected edge appears as two arcs; neighbour lists are strictly
+ *     ascending (so no duplicates); no self-loops. nnz < 2^32, n < 2^24.
+ *   - Distances are 8-bit: 255 means unreachable (Sec. 4.5.1, "Arrays").
+ *   - Vertex ids in and out of the library are the caller's ids. Inside a
+ *     label, hubs are identified by their rank in the vertex order (Sec.
+ *     4.5.1, "Sorting Labels"), so every exported label is sorted by hub.
+ *   - "device" pointers are CUDA global-memory pointers of the current
+ *     device; "host" pointers are ordinary (preferably pinned) host memory.
+ *     The caller owns every buffer it passes in; the library owns the index.
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream). Functions marked "synchronous" wait for that stream
+ *     before they return.
+ *   - Every function returns a pll_status; no C++ exception crosses the ABI.
+ *     On failure no output is valid and nothing is leaked. The library holds
+ *     no global mutable state between calls; an index is immutable after
+ *     pll_build, so queries on one index may run concurrently on different
+ *     streams.
+ */
+#ifndef PLL_H
+#define PLL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PLL_API __attribute__((visibility("default")))
+#else
+#define PLL_API
+#endif
+
+typedef enum pll_status {
+    PLL_OK = 0,
+    PLL_E_INVAL = 1,   /* bad argument or malformed CSR (asymmetric, self-loop,
+                          duplicate or unsorted neighbours, id >= n) */
+    PLL_E_ORDER = 2,   /* order is not a permutation of 0..n-1 */
+    PLL_E_RANGE = 3,   /* a size limit is exceeded (n >= 2^24, t > PLL_MAX_T),
+                          a BFS depth reaches 255, or a finite query distance
+                          is >= 255 */
+    PLL_E_NOMEM = 4,   /* device or host allocation failed */
+    PLL_E_TIMEOUT = 5, /* a bounded device-side wait ran out */
+    PLL_E_CUDA = 6     /* any other CUDA runtime error */
+} pll_status;
+
+/* Largest number of bit-parallel roots (t in Sec. 5.4). */
+#define PLL_MAX_T 64
+
+/* Opaque index: bit-parallel labels L_BP and normal labels L, resident in
+ * device memory of the device that was current at pll_build. */
+typedef struct pll_index pll_index;
+
+/* Build options. Zero-initialise and set what you need. */
+typedef struct pll_build_opts {
+    uint32_t t;          /* bit-parallel roots, 0..PLL_MAX_T (Sec. 5.4). */
+    uint32_t root_batch; /* largest number of pruned-BFS roots processed in
+                            one batch; 0 = library schedule. Any value gives
+                            the same labels. */
+    uint32_t block;      /* threads per CTA of the pruned-BFS kernel (a
+                            multiple of 32, 64..1024); 0 = library default. */
+    uint32_t flags;      /* PLL_BUILD_* bits below. */
+    uint64_t reserved;   /* must be 0. */
+} pll_build_opts;
+
+/* Check the CSR (symmetry, sortedness, self-loops, ranges) before building.
+ * Without it a malformed CSR gives an unspecified (but memory-safe) index. */
+#define PLL_BUILD_VALIDATE 1u
+
+typedef struct pll_stats {
+    uint32_t n;                  /* vertices */
+    uint32_t t;                  /* bit-parallel roots */
+    uint64_t nnz;                /* arcs */
+    uint64_t label_entries;      /* sum over v of |L(v)| (normal labels) */
+    uint64_t pre_cleanup;        /* entries emitted by batched pruned BFSs
+                                    before the redundancy cleanup */
+    uint64_t visited;            /* vertices dequeued by pruned BFSs */
+    uint64_t batches;            /* root batches */
+    uint64_t index_bytes;        /* device bytes held by the index */
+    double ms_prep;              /* order, relabel, root selection */
+    double ms_bp;                /* bit-parallel BFSs */
+    double ms_pruned;            /* pruned BFS + cleanup + append */
+    double ms_finalize;          /* label compaction */
+} pll_stats;
+
+/*
+ * pll_build -- construct the index (Alg. 2 with the bit-parallel stage of
+ * Sec. 5.4; Alg. 1 for each root; Alg. 3 for each bit-parallel root).
+ *
+ *   offsets, cols  device; the graph (see conventions). Read only.
+ *   n, nnz         vertex and arc counts.
+ *   order          device, or NULL. order[r] = vertex of rank r (v_{r+1} in
+ *                  the paper's 1-based notation). NULL selects the Degree
+ *                  strategy of Sec. 4.4.2: descending degree, ties by
+ *                  ascending vertex id.
+ *   opts           build options (t, batching); NULL = t 0, defaults.
+ *   stream         cudaStream_t as void*.
+ *   out            receives the new index; free it with pll_free.
+ *
+ * The labels are the unique ones Alg. 1/2 produce for this order and t,
+ * whatever root_batch and block are. Synchronous. Errors: PLL_E_INVAL,
+ * PLL_E_ORDER, PLL_E_RANGE, PLL_E_NOMEM, PLL_E_CUDA.
+ */
+PLL_API int pll_build(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                      const uint32_t *order, const pll_build_opts *opts, void *stream,
+                      pll_index **out);
+
+/* pll_build_host -- as pll_build, but offsets, cols and order are HOST
+ * pointers; the library copies them to the device inside the call. */
+PLL_API int pll_build_host(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
+                           uint64_t nnz, const uint32_t *order, const pll_build_opts *opts,
+                           void *stream, pll_index **out);
+
+/*
+ * pll_query -- out[i] = d_G(src[i], dst[i]) for i < q: the minimum of the
+ * label query Query(s, t, L) (Sec. 3.3, merge join of hub-sorted labels) and
+ * the bit-parallel query (Sec. 5.3); 255 if s and t are disconnected;
+ * d(s, s) = 0.
+ *
+ *   src, dst   device uint32[q], caller's vertex ids (< n).
+ *   out        device uint8[q].
+ *
+ * Synchronous: waits for the stream, then returns PLL_E_RANGE if some
+ * distance is finite but >= 255 (those entries hold 255) or PLL_E_INVAL if
+ * some id is >= n (those entries hold 255).
+ */
+PLL_API int pll_query(const pll_index *idx, const uint32_t *src, const uint32_t *dst, uint64_t q,
+                      uint8_t *out, void *stream);
+
+/* pll_query_async -- as pll_query but only enqueues the work on the stream.
+ * Range or id errors are counted on the device; pll_query_errors reads and
+ * clears that count (synchronising the stream). */
+PLL_API int pll_query_async(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
+                            uint64_t q, uint8_t *out, void *stream);
+PLL_API int pll_query_errors(const pll_index *idx, void *stream, uint64_t *count);
+
+/* pll_query_host -- as pll_query with HOST src, dst and out; the copies to
+ * and from the device happen inside the call. */
+PLL_API int pll_query_host(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
+                           uint64_t q, uint8_t *out, void *stream);
+
+/*
+ * Exports (synchronous, HOST outputs, indexed by the caller's vertex ids).
+ *
+ * pll_label_entries: *total = sum over v of |L(v)|.
+ * pll_export_labels: offsets[n + 1] (uint64), hubs[total] (hub RANKS,
+ *   ascending within each vertex), dists[total]. Normal labels only
+ *   (Sec. 3.3); the sentinel of Sec. 4.5.2 is not part of the export.
+ * pll_export_bp: vertex-major [n][t] arrays of L_BP (Sec. 5.1): d[v*t + i] =
+ *   d_G(r_i, v) (255 if unreachable), m1 = S^{-1}_{r_i}(v), m0 = S^0_{r_i}(v)
+ *   as 64-bit sets over S_{r_i} (bit j = j-th member in rank order).
+ * pll_export_bp_roots: roots[t] (vertex ids; 0xFFFFFFFF = empty slot),
+ *   cnt[t] = |S_{r_i}|, S[t * 64] = members of S_{r_i} (vertex ids).
+ * pll_export_order: order[n], order[r] = vertex of rank r.
+ */
+PLL_API int pll_label_entries(const pll_index *idx, uint64_t *total);
+PLL_API int pll_export_labels(const pll_index *idx, uint64_t *offsets, uint32_t *hubs,
+                              uint8_t *dists);
+PLL_API int pll_export_bp(const pll_index *idx, uint8_t *d, uint64_t *m1, uint64_t *m0);
+PLL_API int pll_export_bp_roots(const pll_index *idx, uint32_t *roots, uint32_t *cnt,
+                                uint32_t *S);
+PLL_API int pll_export_order(const pll_index *idx, uint32_t *order);
+
+/* Build statistics (sizes, per-phase times in milliseconds). */
+PLL_API int pll_get_stats(const pll_index *idx, pll_stats *out);
+
+/* Release the index and its device memory. NULL is ignored. */
+PLL_API void pll_free(pll_index *idx);
+
+/* Static, human-readable text for a status code. */
+PLL_API const char *pll_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLL_H */

@@ -1,0 +1,218 @@
+"""CPU oracle for Pruned Landmark Labeling -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package. The product
+path (the CUDA library and its binding) never imports it, and it never
+imports the product: the two meet only through the seeded inputs.
+
+``oracle.c`` is a plain single-threaded C restatement of the paper:
+the Degree order (Sec. 4.4.2), bit-parallel labels (Alg. 3, Sec. 5),
+the pruned BFSs of Alg. 1/2 with bit-parallel pruning (Sec. 5.4), the
+label query (Sec. 3.3, Sec. 5.3), plain BFS, and the closed form of one
+label derived from Thm 4.1 / Thm 4.2 (see the header of oracle.c).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "oracle.c"
+SO = HERE / "liboracle.so"
+
+OK, E_INVAL, E_ORDER, E_RANGE, E_NOMEM = 0, 1, 2, 3, 4
+INF = 255
+BPW = 64
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (plain -O2; no vector intrinsics)."""
+    if force or not SO.exists() or SO.stat().st_mtime < SRC.stat().st_mtime:
+        tmp = SO.with_suffix(f".so.tmp{os.getpid()}")
+        r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", str(tmp), str(SRC)],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+        os.replace(tmp, SO)
+    return str(SO)
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        vp, u32, u64, i32, i64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int, C.c_int64
+        lib.orc_degree_order.restype = i32
+        lib.orc_degree_order.argtypes = [u32, vp, vp, vp]
+        lib.orc_bfs.restype = i32
+        lib.orc_bfs.argtypes = [u32, vp, vp, u32, vp]
+        lib.orc_build.restype = vp
+        lib.orc_build.argtypes = [u32, vp, vp, vp, u32, C.POINTER(C.c_int)]
+        lib.orc_free.restype = None
+        lib.orc_free.argtypes = [vp]
+        lib.orc_query.restype = i32
+        lib.orc_query.argtypes = [vp, u32, u32]
+        lib.orc_query_batch.restype = i32
+        lib.orc_query_batch.argtypes = [vp, u64, vp, vp, vp]
+        lib.orc_total_entries.restype = u64
+        lib.orc_total_entries.argtypes = [vp]
+        lib.orc_export_labels.restype = None
+        lib.orc_export_labels.argtypes = [vp, vp, vp, vp]
+        lib.orc_export_bp.restype = None
+        lib.orc_export_bp.argtypes = [vp, vp, vp, vp]
+        lib.orc_export_bp_roots.restype = None
+        lib.orc_export_bp_roots.argtypes = [vp, vp, vp, vp]
+        lib.orc_export_order.restype = None
+        lib.orc_export_order.argtypes = [vp, vp]
+        lib.orc_counters.restype = None
+        lib.orc_counters.argtypes = [vp, vp]
+        lib.orc_label_of.restype = i64
+        lib.orc_label_of.argtypes = [u32, vp, vp, vp, vp, u32, vp, vp]
+        lib.orc_export_rank_inX.restype = None
+        lib.orc_export_rank_inX.argtypes = [vp, vp, vp]
+        _lib = lib
+    return _lib
+
+
+def _u32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__(f"oracle status {code} {what}")
+        self.code = code
+
+
+def degree_order(offsets, cols) -> np.ndarray:
+    off, col = _u32(offsets), _u32(cols)
+    n = off.shape[0] - 1
+    out = np.empty(max(n, 1), dtype=np.uint32)
+    st = _load().orc_degree_order(n, off.ctypes.data, col.ctypes.data, out.ctypes.data)
+    if st:
+        raise OracleError(st, "degree_order")
+    return out[:n]
+
+
+def bfs(offsets, cols, src: int) -> np.ndarray:
+    off, col = _u32(offsets), _u32(cols)
+    n = off.shape[0] - 1
+    out = np.empty(max(n, 1), dtype=np.uint8)
+    st = _load().orc_bfs(n, off.ctypes.data, col.ctypes.data, src, out.ctypes.data)
+    if st:
+        raise OracleError(st, "bfs")
+    return out[:n]
+
+
+@dataclass
+class Labels:
+    offsets: np.ndarray  # uint64 [n + 1], by vertex id
+    hubs: np.ndarray     # uint32 hub ranks, ascending within a vertex
+    dists: np.ndarray    # uint8
+
+
+class Index:
+    """Index built by the oracle (Alg. 3 then Alg. 2/1)."""
+
+    def __init__(self, offsets, cols, t: int, order=None):
+        self._off, self._col = _u32(offsets), _u32(cols)
+        self.n = self._off.shape[0] - 1
+        self.t = t
+        lib = _load()
+        st = C.c_int(0)
+        ordp = None
+        if order is not None:
+            self._ord = _u32(order)
+            ordp = self._ord.ctypes.data
+        self._h = lib.orc_build(self.n, self._off.ctypes.data, self._col.ctypes.data, ordp, t,
+                                C.byref(st))
+        if not self._h:
+            raise OracleError(st.value, "build")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _load().orc_free(h)
+            self._h = None
+
+    def query(self, s: int, u: int) -> int:
+        d = _load().orc_query(self._h, s, u)
+        if d < 0:
+            raise OracleError(-d, "query")
+        return d
+
+    def query_batch(self, s, u) -> np.ndarray:
+        s, u = _u32(s), _u32(u)
+        out = np.empty(max(s.shape[0], 1), dtype=np.uint8)
+        st = _load().orc_query_batch(self._h, s.shape[0], s.ctypes.data, u.ctypes.data, out.ctypes.data)
+        if st:
+            raise OracleError(st, "query_batch")
+        return out[: s.shape[0]]
+
+    def labels(self) -> Labels:
+        lib = _load()
+        tot = lib.orc_total_entries(self._h)
+        off = np.empty(self.n + 1, dtype=np.uint64)
+        hubs = np.empty(max(tot, 1), dtype=np.uint32)
+        dists = np.empty(max(tot, 1), dtype=np.uint8)
+        lib.orc_export_labels(self._h, off.ctypes.data, hubs.ctypes.data, dists.ctypes.data)
+        return Labels(off, hubs[:tot], dists[:tot])
+
+    def bp(self):
+        nt = max(self.n * self.t, 1)
+        d = np.empty(nt, dtype=np.uint8)
+        m1 = np.empty(nt, dtype=np.uint64)
+        m0 = np.empty(nt, dtype=np.uint64)
+        _load().orc_export_bp(self._h, d.ctypes.data, m1.ctypes.data, m0.ctypes.data)
+        k = self.n * self.t
+        shp = (self.n, self.t)
+        return d[:k].reshape(shp), m1[:k].reshape(shp), m0[:k].reshape(shp)
+
+    def bp_roots(self):
+        t = max(self.t, 1)
+        roots = np.empty(t, dtype=np.uint32)
+        cnt = np.empty(t, dtype=np.uint32)
+        S = np.empty(t * BPW, dtype=np.uint32)
+        _load().orc_export_bp_roots(self._h, roots.ctypes.data, cnt.ctypes.data, S.ctypes.data)
+        return roots[: self.t], cnt[: self.t], S[: self.t * BPW].reshape(self.t, BPW)
+
+    def order(self) -> np.ndarray:
+        out = np.empty(max(self.n, 1), dtype=np.uint32)
+        _load().orc_export_order(self._h, out.ctypes.data)
+        return out[: self.n]
+
+    def rank_inX(self):
+        rank = np.empty(max(self.n, 1), dtype=np.uint32)
+        inX = np.empty(max(self.n, 1), dtype=np.uint8)
+        _load().orc_export_rank_inX(self._h, rank.ctypes.data, inX.ctypes.data)
+        return rank[: self.n], inX[: self.n]
+
+    def counters(self) -> dict:
+        out = np.zeros(4, dtype=np.uint64)
+        _load().orc_counters(self._h, out.ctypes.data)
+        return dict(visited=int(out[0]), labeled=int(out[1]), scanned=int(out[2]),
+                    labeled_deg=int(out[3]))
+
+
+def label_of(offsets, cols, rank, inX, u: int):
+    """Closed-form L(u) for the order given by `rank` and bit-parallel set `inX`:
+    returns (hub ranks ascending, distances)."""
+    off, col = _u32(offsets), _u32(cols)
+    n = off.shape[0] - 1
+    rank = _u32(rank)
+    inX = np.ascontiguousarray(np.asarray(inX, dtype=np.uint8))
+    hubs = np.empty(max(n, 1), dtype=np.uint32)
+    dists = np.empty(max(n, 1), dtype=np.uint8)
+    c = _load().orc_label_of(n, off.ctypes.data, col.ctypes.data, rank.ctypes.data, inX.ctypes.data,
+                             u, hubs.ctypes.data, dists.ctypes.data)
+    if c < 0:
+        raise OracleError(-c, "label_of")
+    return hubs[:c].copy(), dists[:c].copy()

@@ -1,0 +1,157 @@
+"""Seeded synthetic inputs: graphs (uint32 CSR) and uniform query pairs.
+
+Thin ctypes front end of ``csrc/graphgen.c``. The generators hold none of the
+labelling method's arithmetic; both the CUDA library and the CPU oracle take
+their output as plain arrays. Graph families stand in for the power-law,
+small-world networks the paper evaluates on (Sec. 6.1, Table 3):
+Barabasi-Albert, Watts-Strogatz (high diameter) and R-MAT.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build_graphgen()
+        lib = C.CDLL(path)
+        vp, u32, u64, dbl = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
+        lib.gg_from_edges.restype = vp
+        lib.gg_from_edges.argtypes = [u32, u64, vp, vp]
+        lib.gg_ba.restype = vp
+        lib.gg_ba.argtypes = [u32, u32, u64]
+        lib.gg_ws.restype = vp
+        lib.gg_ws.argtypes = [u32, u32, dbl, u64]
+        lib.gg_rmat.restype = vp
+        lib.gg_rmat.argtypes = [u32, u32, dbl, dbl, dbl, u64]
+        lib.gg_n.restype = u32
+        lib.gg_n.argtypes = [vp]
+        lib.gg_nnz.restype = u64
+        lib.gg_nnz.argtypes = [vp]
+        lib.gg_copy.restype = None
+        lib.gg_copy.argtypes = [vp, vp, vp]
+        lib.gg_free.restype = None
+        lib.gg_free.argtypes = [vp]
+        lib.gg_pairs.restype = None
+        lib.gg_pairs.argtypes = [u32, u64, u64, vp, vp]
+        lib.gg_uniform.restype = None
+        lib.gg_uniform.argtypes = [u64, u64, vp]
+        lib.gg_below.restype = None
+        lib.gg_below.argtypes = [u64, u64, u64, vp]
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Graph:
+    """Undirected simple graph as a symmetric CSR (sorted neighbour lists)."""
+
+    n: int
+    offsets: np.ndarray  # uint32 [n + 1]
+    cols: np.ndarray     # uint32 [nnz]
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.cols.shape[0])
+
+    @property
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.offsets.astype(np.int64))
+
+
+def _take(handle, name) -> Graph:
+    lib = _load()
+    if not handle:
+        raise MemoryError(f"graph generator failed for {name}")
+    try:
+        n = lib.gg_n(handle)
+        nnz = lib.gg_nnz(handle)
+        off = np.empty(n + 1, dtype=np.uint32)
+        col = np.empty(max(nnz, 1), dtype=np.uint32)
+        lib.gg_copy(handle, off.ctypes.data, col.ctypes.data)
+    finally:
+        lib.gg_free(handle)
+    return Graph(n, off, col[:nnz].copy(), name)
+
+
+def from_edges(n: int, u, v, name: str = "edges") -> Graph:
+    """Symmetrised simple graph on n vertices from an edge list."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.uint32))
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.uint32))
+    assert u.shape == v.shape
+    h = _load().gg_from_edges(n, u.shape[0], u.ctypes.data, v.ctypes.data)
+    return _take(h, name)
+
+
+def ba(n: int, m: int, seed: int) -> Graph:
+    return _take(_load().gg_ba(n, m, seed), f"ba(n={n},m={m},seed={seed})")
+
+
+def ws(n: int, k: int, p: float, seed: int) -> Graph:
+    return _take(_load().gg_ws(n, k, p, seed), f"ws(n={n},k={k},p={p},seed={seed})")
+
+
+def rmat(scale: int, ef: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = 1) -> Graph:
+    return _take(_load().gg_rmat(scale, ef, a, b, c, seed),
+                 f"rmat(scale={scale},ef={ef},seed={seed})")
+
+
+def pairs(n: int, q: int, seed: int):
+    """q uniform query pairs (s, t) in [0, n)^2 as two uint32 arrays."""
+    s = np.empty(max(q, 1), dtype=np.uint32)
+    t = np.empty(max(q, 1), dtype=np.uint32)
+    if q:
+        _load().gg_pairs(n, q, seed, s.ctypes.data, t.ctypes.data)
+    return s[:q], t[:q]
+
+
+def uniform(seed: int, count: int) -> np.ndarray:
+    out = np.empty(max(count, 1), dtype=np.float64)
+    if count:
+        _load().gg_uniform(seed, count, out.ctypes.data)
+    return out[:count]
+
+
+def below(seed: int, count: int, bound: int) -> np.ndarray:
+    out = np.empty(max(count, 1), dtype=np.uint64)
+    if count:
+        _load().gg_below(seed, count, bound, out.ctypes.data)
+    return out[:count]
+
+
+def batch_specs(count: int = 256, seed: int = 4, n_lo: int = 1000, n_hi: int = 50000):
+    """The uneven multi-graph workload: half Barabasi-Albert (n log-uniform on
+    [n_lo, n_hi], m uniform in 2..8), half Watts-Strogatz (n log-uniform on
+    [n_lo, n_hi], k = 6, p = 0.1). Returns a list of (kind, n, param, seed)."""
+    u = uniform(seed, 2 * count)
+    ms = below(seed + 1, count, 7)
+    specs = []
+    lo, hi = math.log(n_lo), math.log(n_hi)
+    for i in range(count):
+        n = int(math.floor(math.exp(lo + (hi - lo) * float(u[i]))))
+        n = max(n_lo, min(n_hi, n))
+        if i < count // 2:
+            specs.append(("ba", n, int(ms[i]) + 2, 10_000 + i))
+        else:
+            specs.append(("ws", n, 6, 20_000 + i))
+    return specs
+
+
+def make(spec) -> Graph:
+    kind, n, param, seed = spec
+    if kind == "ba":
+        return ba(n, param, seed)
+    if kind == "ws":
+        return ws(n, param, 0.1, seed)
+    raise ValueError(kind)

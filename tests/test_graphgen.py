@@ -1,0 +1,74 @@
+"""Input generators: CSR invariants, determinism, family shapes (no GPU)."""
+import numpy as np
+import pytest
+
+from paper_1304_4661_gb300 import graphgen as gg
+
+
+def check_csr(g):
+    off = g.offsets.astype(np.int64)
+    assert off[0] == 0 and (np.diff(off) >= 0).all() and off[-1] == g.nnz
+    rows = np.repeat(np.arange(g.n), np.diff(off))
+    cols = g.cols.astype(np.int64)
+    assert (cols < g.n).all()
+    assert (rows != cols).all(), "self-loop"
+    # strictly ascending within each list
+    same = rows[1:] == rows[:-1]
+    assert (cols[1:][same] > cols[:-1][same]).all(), "unsorted or duplicate"
+    # symmetric
+    fwd = np.sort(rows * g.n + cols)
+    bwd = np.sort(cols * g.n + rows)
+    assert np.array_equal(fwd, bwd), "asymmetric"
+
+
+@pytest.mark.parametrize("make", [
+    lambda: gg.ba(10_000, 4, 1),
+    lambda: gg.ws(5_000, 6, 0.1, 2),
+    lambda: gg.rmat(14, 16, seed=3),
+    lambda: gg.ba(3, 4, 1),
+    lambda: gg.from_edges(5, [0, 1, 1, 3], [1, 0, 1, 4]),
+])
+def test_csr_invariants(make):
+    check_csr(make())
+
+
+def test_ba_shape():
+    g = gg.ba(10_000, 4, 1)
+    # (m+1)-clique plus m edges per new vertex, all distinct
+    assert g.nnz == 2 * (10 + (10_000 - 5) * 4)
+    assert g.degrees.min() >= 4
+
+
+def test_ws_shape():
+    g = gg.ws(1000, 6, 0.1, 5)
+    assert g.nnz == 2 * 1000 * 3  # rewiring keeps the edge count
+    assert g.degrees.min() >= 1
+
+
+def test_rmat_shape():
+    g = gg.rmat(12, 16, seed=1)
+    assert g.n == 4096
+    assert g.nnz <= 2 * 16 * 4096
+    # power-law-ish: max degree far above the mean; many isolated vertices
+    d = g.degrees
+    assert d.max() > 20 * d.mean()
+    assert (d == 0).sum() > 0
+
+
+def test_determinism():
+    a, b = gg.rmat(11, 8, seed=7), gg.rmat(11, 8, seed=7)
+    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.cols, b.cols)
+    c = gg.rmat(11, 8, seed=8)
+    assert not np.array_equal(a.cols[: min(a.nnz, c.nnz)], c.cols[: min(a.nnz, c.nnz)])
+    s1, t1 = gg.pairs(1000, 100, 2)
+    s2, t2 = gg.pairs(1000, 100, 2)
+    assert np.array_equal(s1, s2) and np.array_equal(t1, t2)
+    assert s1.max() < 1000 and t1.max() < 1000
+
+
+def test_batch_specs():
+    specs = gg.batch_specs()
+    assert len(specs) == 256
+    assert sum(1 for s in specs if s[0] == "ba") == 128
+    assert all(1000 <= s[1] <= 50000 for s in specs)
+    assert all(2 <= s[2] <= 8 for s in specs if s[0] == "ba")
