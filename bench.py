@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Benchmark of the PLL hot path on one GB300: index build + batched queries.
+
+One step = the whole path over one synthetic graph: pll_build (CSR checks,
+Degree order, relabel, bit-parallel stage, batched pruned BFS + cleanup,
+compaction) followed by pll_query over the workload's uniform pairs. Inputs
+are resident in HBM before the timed region; every step builds a fresh index.
+
+Prints ONE JSON line (rank 0). `value` is the index build time in seconds of
+the named workload (lower is better); queries/s and the query p99 latency sit
+beside it. `e2e` repeats the step through the host-pointer entry points
+(pll_build_host, pll_query_host) with the host<->device copies inside the
+timed region. `--impl reference` times the CPU oracle instead (a bounded
+sample of the same workload; see its `sample` field).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PLL build s + queries/s, p99 us on R-MAT-20; learned/served vs plain GPU"
+
+WORKLOADS = {
+    # R-MAT scale 20, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05), graph seed 1,
+    # Degree order, t = 64, 10M uniform pairs (seed 3)
+    "rmat20": dict(kind="rmat", scale=20, ef=16, t=64, queries=10_000_000, graph_seed=1, pair_seed=3),
+    # Barabasi-Albert n = 10,000, m = 4, seed 1, t = 16, 100k pairs (seed 2)
+    "ba10k": dict(kind="ba", n=10_000, m=4, t=16, queries=100_000, graph_seed=1, pair_seed=2),
+    # small R-MAT for quick runs
+    "rmat16": dict(kind="rmat", scale=16, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
+}
+
+# DRAM bytes per launch of the pruned-BFS kernel measured by ncu, valid only
+# for the kernel source with this hash (else traffic is reported as null).
+PROFILED = {}
+
+
+def make_graph(w):
+    from paper_1304_4661_gb300 import graphgen as gg
+    if w["kind"] == "rmat":
+        return gg.rmat(w["scale"], w["ef"], seed=w["graph_seed"])
+    return gg.ba(w["n"], w["m"], w["graph_seed"])
+
+
+def _workload_name(w):
+    if w["kind"] == "rmat":
+        return f"R-MAT scale {w['scale']} ef {w['ef']} (a,b,c,d)=(.57,.19,.19,.05) seed {w['graph_seed']}"
+    return f"Barabasi-Albert n={w['n']} m={w['m']} seed {w['graph_seed']}"
+
+
+def describe(w, g):
+    return {"workload": _workload_name(w), "n": g.n, "arcs": g.nnz, "t": w["t"], "order": "degree (ties by id)",
+            "queries": w["queries"], "pair_seed": w["pair_seed"],
+            "l2": "L2 flushed (512 MiB write) between timed steps"}
+
+
+def file_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, w, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+    g = make_graph(w)
+    s, u = gg.pairs(g.n, w["queries"], w["pair_seed"])
+    t = w["t"]
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    off_d, col_d, s_d, u_d = dev(g.offsets), dev(g.cols), dev(s), dev(u)
+    out_d = torch.empty(w["queries"], dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ix = pll.Index.build(off_d, col_d, t=t, root_batch=args.root_batch, block=args.block)
+        e1.record(stream)
+        ix.query(s_d, u_d, out_d)
+        e2.record(stream)
+        e2.synchronize()
+        st = ix.stats()
+        ix.close()
+        if record is not None:
+            record.append((e0.elapsed_time(e1), e1.elapsed_time(e2), st))
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step(None)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    recs = []
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        step(recs)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+
+    build_ms = statistics.mean(r[0] for r in recs)
+    query_ms = statistics.mean(r[1] for r in recs)
+    step_ms = build_ms + query_ms
+    build_ms = max_over_ranks(ws, build_ms)
+    step_ms = max_over_ranks(ws, step_ms)
+    st = recs[-1][2]
+
+    # per-pair latency through the synchronous C-ABI query (host wall clock)
+    ix = pll.Index.build(off_d, col_d, t=t)
+    lat = []
+    one_out = torch.empty(1, dtype=torch.uint8, device="cuda")
+    for i in range(args.latency_samples):
+        a, b = s_d[i:i + 1], u_d[i:i + 1]
+        torch.cuda.synchronize()
+        tq = time.perf_counter()
+        ix.query(a, b, one_out)
+        lat.append((time.perf_counter() - tq) * 1e6)
+    lat.sort()
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    # query kernel alone: one launch, CUDA events on the launching stream
+    qk = []
+    for _ in range(3):
+        flush.fill_(1)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ix.query_async(s_d, u_d, out_d)
+        a1.record(stream)
+        a1.synchronize()
+        qk.append(a0.elapsed_time(a1))
+    assert ix.query_errors() == 0
+    qk_ms = statistics.mean(qk)
+    lab = ix.labels()
+    Lsz = np.diff(lab.offsets.astype(np.int64))
+    ix.close()
+
+    # ---- e2e through the host-pointer entry points
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).pin_memory()
+        off_h, col_h, s_h, u_h = pin(g.offsets), pin(g.cols), pin(s), pin(u)
+        res_h = torch.empty(w["queries"], dtype=torch.uint8).pin_memory()
+        off_n, col_n = off_h.numpy().view(np.uint32), col_h.numpy().view(np.uint32)
+        s_n, u_n, res_n = s_h.numpy().view(np.uint32), u_h.numpy().view(np.uint32), res_h.numpy()
+        lib = pll.load()
+        import ctypes as C
+        times_b, times_q = [], []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            tb = time.perf_counter()
+            opts = pll.BuildOpts(t, args.root_batch, args.block, 0, 0)
+            h = C.c_void_p()
+            rc = lib.pll_build_host(off_n.ctypes.data, col_n.ctypes.data, g.n, g.nnz, None,
+                                    C.byref(opts), None, C.byref(h))
+            assert rc == 0, pll.status_str(rc)
+            tm = time.perf_counter()
+            rc = lib.pll_query_host(h.value, s_n.ctypes.data, u_n.ctypes.data, w["queries"],
+                                    res_n.ctypes.data, None)
+            assert rc == 0, pll.status_str(rc)
+            te = time.perf_counter()
+            lib.pll_free(h.value)
+            if it >= args.warmup:
+                times_b.append(tm - tb)
+                times_q.append(te - tm)
+        assert np.array_equal(res_n, out_d.cpu().numpy())
+        e2e = {"value": round(statistics.mean(times_b), 6), "unit": "s",
+               "queries_per_s": round(w["queries"] / statistics.mean(times_q), 1),
+               "step_s": round(statistics.mean(times_b) + statistics.mean(times_q), 6),
+               "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.nnz + 8 * w["queries"]),
+               "d2h_bytes_per_step": int(w["queries"])}
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / event time)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    launches = max(st["pruned_launches"], 1)
+    pr_bytes = (st["visited"] * (8 + 12 + t) + st["pruned_masks"] * 16 + st["pruned_scanned"] * 4
+                + st["pruned_expanded"] * 8 + st["pre_cleanup"] * 8)
+    pr_ms = st["ms_pruned_kernel"]
+    q = w["queries"]
+    # per pair: ids (8), ranks (8), 2 x t distance bytes, 4 label offsets (32),
+    # the result byte, and both labels (4 bytes per entry; Lsz is by vertex id)
+    q_bytes = q * (8 + 8 + 2 * t + 32 + 1) + 4 * int(Lsz[s].sum() + Lsz[u].sum())
+    kern = {
+        "k_pruned_batch": {"ms_per_step": pr_ms, "launches": st["pruned_launches"],
+                           "bytes_per_launch": pr_bytes / launches,
+                           "ms_per_launch": pr_ms / launches},
+        "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes_per_launch": q_bytes,
+                    "ms_per_launch": qk_ms},
+    }
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    kd = kern[dom]
+    achieved = kd["bytes_per_launch"] / (kd["ms_per_launch"] * 1e-3) / 1e9
+    src = os.path.join(ROOT, "paper_1304_4661_gb300", "csrc",
+                       "k_pruned.cu" if dom == "k_pruned_batch" else "k_query.cu")
+    prof = PROFILED.get(dom)
+    traffic = prof["dram_bytes_per_launch"] if prof and prof["src_sha"] == file_sha(src) else None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": traffic,
+                "others": {k: {"achieved_gbs": round(v["bytes_per_launch"] / (v["ms_per_launch"] * 1e-3) / 1e9, 1),
+                               "ms_per_step": round(v["ms_per_step"], 3), "launches": v["launches"]}
+                           for k, v in kern.items()}}
+
+    out = {
+        "metric": METRIC, "value": round(build_ms / 1e3, 6), "unit": "s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": describe(w, g),
+        "build_s": round(build_ms / 1e3, 6),
+        "queries_per_s": round(q / (query_ms * 1e-3), 1),
+        "query_kernel_ms": round(qk_ms, 3),
+        "query_p50_us": round(p50, 2), "query_p99_us": round(p99, 2),
+        "latency_note": "per single-pair synchronous pll_query call, host wall clock",
+        "label_entries": st["label_entries"],
+        "label_entries_per_s": round(st["label_entries"] / (build_ms * 1e-3), 1),
+        "avg_label": round(st["label_entries"] / max(g.n, 1), 2),
+        "phases_ms": {"prep": round(st["ms_prep"], 3), "bp": round(st["ms_bp"], 3),
+                      "pruned": round(st["ms_pruned"], 3), "pruned_kernel": round(st["ms_pruned_kernel"], 3),
+                      "finalize": round(st["ms_finalize"], 3)},
+        "batches": st["batches"], "pre_cleanup": st["pre_cleanup"], "visited": st["visited"],
+        "wall_s_timed_region": round(wall, 3),
+        "clocks": clk, "e2e": e2e, "roofline": roofline,
+        "gpu_launches": int(args.steps * (st["launches"] + 1)),
+        "cub_calls_per_step": st["cub_calls"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_baseline(args, scale=None):
+    """The oracle as it stands (single thread) on a bounded sample: a full
+    index build of a smaller R-MAT of the same family, plus 1M queries."""
+    import oracle
+    from paper_1304_4661_gb300 import graphgen as gg
+    scale = scale or args.cpu_scale
+    g = gg.rmat(scale, 16, seed=1)
+    t0 = time.perf_counter()
+    ix = oracle.Index(g.offsets, g.cols, 64)
+    tb = time.perf_counter() - t0
+    s, u = gg.pairs(g.n, 1_000_000, 3)
+    t1 = time.perf_counter()
+    ix.query_batch(s, u)
+    tq = time.perf_counter() - t1
+    return {"value": round(tb, 3), "unit": "s", "cores": 1, "kind": "oracle",
+            "queries_per_s": round(1_000_000 / tq, 1),
+            "sample": f"full oracle build of R-MAT scale {scale} (ef 16, seed 1, t=64, "
+                      f"{g.n} vertices, {g.nnz} arcs), then 1M uniform queries; single thread"}
+
+
+def run_reference(args, w, ws, rank):
+    """The CPU oracle as the reference arm, each step a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1304_4661_gb300 import graphgen as gg
+    scale = args.ref_scale
+    g = gg.rmat(scale, 16, seed=1)
+    s, u = gg.pairs(g.n, 200_000, 3)
+    bt, qt = [], []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ix = oracle.Index(g.offsets, g.cols, 64)
+        t1 = time.perf_counter()
+        ix.query_batch(s, u)
+        t2 = time.perf_counter()
+        del ix
+        if it >= args.warmup:
+            bt.append(t1 - t0)
+            qt.append(t2 - t1)
+    v = statistics.mean(bt)
+    sample = (f"oracle full build of R-MAT scale {scale} (ef 16, seed 1, t=64, {g.n} vertices, "
+              f"{g.nnz} arcs) + 200k queries per step; single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round((v + statistics.mean(qt)) * 1e3, 3), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "config": {"workload": _workload_name(w), "sample": sample},
+           "queries_per_s": round(200_000 / statistics.mean(qt), 1),
+           "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--root-batch", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--latency-samples", type=int, default=2000)
+    ap.add_argument("--cpu-scale", type=int, default=17)
+    ap.add_argument("--ref-scale", type=int, default=15)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_setup() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        run_reference(args, w, ws, rank)
+        return
+    run_ours(args, w, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,15 +69,11 @@ typedef struct pll_build_opts {
     uint32_t root_batch; /* largest number of pruned-BFS roots processed in
                             one batch; 0 = library schedule. Any value gives
                             the same labels. */
-    uint32_t block;      /* threads per CTA of the pruned-BFS kernel (a
-                            multiple of 32, 64..1024); 0 = library default. */
-    uint32_t flags;      /* PLL_BUILD_* bits below. */
+    uint32_t block;      /* threads per CTA of the pruned-BFS kernel: 128,
+                            256 or 512; 0 = library default (256). */
+    uint32_t flags;      /* reserved, must be 0. */
     uint64_t reserved;   /* must be 0. */
 } pll_build_opts;
-
-/* Check the CSR (symmetry, sortedness, self-loops, ranges) before building.
- * Without it a malformed CSR gives an unspecified (but memory-safe) index. */
-#define PLL_BUILD_VALIDATE 1u
 
 typedef struct pll_stats {
     uint32_t n;                  /* vertices */
@@ -91,8 +87,17 @@ typedef struct pll_stats {
     uint64_t index_bytes;        /* device bytes held by the index */
     double ms_prep;              /* order, relabel, root selection */
     double ms_bp;                /* bit-parallel BFSs */
-    double ms_pruned;            /* pruned BFS + cleanup + append */
-    double ms_finalize;          /* label compaction */
+    double ms_pruned;            /* pruned BFS + cleanup + append + compaction */
+    double ms_finalize;          /* label compaction (part of ms_pruned) */
+    /* work of the pruned-BFS kernel, summed over its launches */
+    double ms_pruned_kernel;     /* CUDA-event time of the pruned-BFS launches */
+    uint64_t pruned_launches;    /* its launches */
+    uint64_t pruned_scanned;     /* label entries read by prune tests */
+    uint64_t pruned_masks;       /* bit-parallel mask pairs read by prune tests */
+    uint64_t pruned_expanded;    /* arcs scanned from unpruned vertices */
+    uint64_t launches;           /* kernels of this library launched by the build
+                                    (not counting CUB's) */
+    uint64_t cub_calls;          /* CUB device-wide sorts, scans, selects */
 } pll_stats;
 
 /*
@@ -109,6 +114,8 @@ typedef struct pll_stats {
  *   stream         cudaStream_t as void*.
  *   out            receives the new index; free it with pll_free.
  *
+ * The CSR is always checked first (offsets, ids, self-loops, strict ascent,
+ * symmetry); a malformed graph gives PLL_E_INVAL and no index.
  * The labels are the unique ones Alg. 1/2 produce for this order and t,
  * whatever root_batch and block are. Synchronous. Errors: PLL_E_INVAL,
  * PLL_E_ORDER, PLL_E_RANGE, PLL_E_NOMEM, PLL_E_CUDA.

@@ -56,6 +56,8 @@ def _load():
         lib.orc_bfs.argtypes = [u32, vp, vp, u32, vp]
         lib.orc_build.restype = vp
         lib.orc_build.argtypes = [u32, vp, vp, vp, u32, C.POINTER(C.c_int)]
+        lib.orc_build_ex.restype = vp
+        lib.orc_build_ex.argtypes = [u32, vp, vp, vp, u32, i32, C.POINTER(C.c_int)]
         lib.orc_free.restype = None
         lib.orc_free.argtypes = [vp]
         lib.orc_query.restype = i32
@@ -122,7 +124,7 @@ class Labels:
 class Index:
     """Index built by the oracle (Alg. 3 then Alg. 2/1)."""
 
-    def __init__(self, offsets, cols, t: int, order=None):
+    def __init__(self, offsets, cols, t: int, order=None, with_pruned: bool = True):
         self._off, self._col = _u32(offsets), _u32(cols)
         self.n = self._off.shape[0] - 1
         self.t = t
@@ -132,8 +134,8 @@ class Index:
         if order is not None:
             self._ord = _u32(order)
             ordp = self._ord.ctypes.data
-        self._h = lib.orc_build(self.n, self._off.ctypes.data, self._col.ctypes.data, ordp, t,
-                                C.byref(st))
+        self._h = lib.orc_build_ex(self.n, self._off.ctypes.data, self._col.ctypes.data, ordp, t,
+                                   1 if with_pruned else 0, C.byref(st))
         if not self._h:
             raise OracleError(st.value, "build")
 

@@ -265,8 +265,10 @@ void orc_free(orc_index *ix) {
 }
 
 /* ------------------------- Alg. 2 + Alg. 1 with the Sec. 5.4 combination */
-orc_index *orc_build(uint32_t n, const uint32_t *off, const uint32_t *col,
-                     const uint32_t *order, uint32_t t, int *status) {
+/* with_pruned = 0 stops after the bit-parallel stage (order, X and L_BP only),
+ * for checks of single labels on graphs too large for the whole Alg. 2. */
+orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
+                        const uint32_t *order, uint32_t t, int with_pruned, int *status) {
     int st = ORC_OK;
     orc_index *ix = (orc_index *)calloc(1, sizeof(orc_index));
     if (!ix) { *status = ORC_E_NOMEM; return NULL; }
@@ -318,7 +320,7 @@ orc_index *orc_build(uint32_t n, const uint32_t *off, const uint32_t *col,
     free(Sm1); Sm1 = NULL; free(S0); S0 = NULL; free(E0); E0 = NULL; free(E1); E1 = NULL;
 
     /* pruned stage: Alg. 2 calls PrunedBFS(G, v_k, L'_{k-1}) for k = 1..n */
-    {
+    if (with_pruned) {
         uint8_t *T = (uint8_t *)malloc((size_t)n + 1);     /* root array T (Sec. 4.5.1) */
         uint8_t *Pd = (uint8_t *)malloc((size_t)n + 1);    /* tentative distances P */
         uint32_t *visited = Q1;                            /* for the lazy reset */
@@ -372,6 +374,11 @@ done:
     if (st) { orc_free(ix); *status = st; return NULL; }
     *status = ORC_OK;
     return ix;
+}
+
+orc_index *orc_build(uint32_t n, const uint32_t *off, const uint32_t *col,
+                     const uint32_t *order, uint32_t t, int *status) {
+    return orc_build_ex(n, off, col, order, t, 1, status);
 }
 
 /* Query(s, t, L) of Sec. 3.3 by merge join over hub-sorted labels, combined

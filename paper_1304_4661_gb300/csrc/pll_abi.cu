@@ -1,0 +1,570 @@
+// pll_abi.cu -- the C ABI of include/pll.h and the host side of the build.
+//
+// pll_build runs, on the caller's stream:
+//   1. CSR checks, vertex order (given, or the Degree strategy of Sec. 4.4.2),
+//      relabelling into rank space;
+//   2. the greedy bit-parallel root choice and t bit-parallel BFSs (Sec. 5.4,
+//      Alg. 3);
+//   3. Alg. 2 over batches of roots [k0, k1): one pruned-BFS launch for the
+//      whole batch (Alg. 1 per root, pruned with hubs < k0 and the
+//      bit-parallel labels), then sort + redundancy cleanup + append of the
+//      batch's entries; batch sizes double from 32 up to root_batch;
+//   4. compaction of the labels into one hub-sorted CSR for queries.
+// The host reads two small counter blocks per batch (emitted-tuple count and
+// error bits; entries kept); everything else stays on the device.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pll_internal.cuh"
+
+namespace pll {
+
+int cuda_status(cudaError_t e) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PLL_E_NOMEM : PLL_E_CUDA;
+}
+
+namespace {
+
+struct Counters {
+    unsigned long long out_cnt;
+    unsigned long long nkept;
+    unsigned long long visit_cnt;
+    unsigned long long pool_top;
+    unsigned long long work[3];  // scanned, masks, expanded (cumulative)
+    uint32_t next_root;
+    uint32_t err;
+};
+
+int err_to_status(uint32_t err) {
+    if (err & ERR_CSR) return PLL_E_INVAL;
+    if (err & ERR_ORDER) return PLL_E_ORDER;
+    if (err & ERR_DEPTH) return PLL_E_RANGE;
+    if (err & ERR_POOL) return PLL_E_NOMEM;
+    return PLL_OK;
+}
+
+int read_err(uint32_t *d_err, cudaStream_t s, uint32_t *h) {
+    PLL_TRY(cudaMemcpyAsync(h, d_err, 4, cudaMemcpyDeviceToHost, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    return PLL_OK;
+}
+
+int bit_length(uint32_t x) {
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+void free_index(pll_index *ix) {
+    if (!ix) return;
+    cudaFree(ix->d_order);
+    cudaFree(ix->d_inv);
+    cudaFree(ix->d_bp_d);
+    cudaFree(ix->d_bp_m);
+    cudaFree(ix->d_bp_root);
+    cudaFree(ix->d_bp_cnt);
+    cudaFree(ix->d_bp_S);
+    cudaFree(ix->d_lab_off);
+    cudaFree(ix->d_lab);
+    cudaFree(ix->d_qerr);
+    delete ix;
+}
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Timer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, s); }
+    double stop_ms() {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+};
+
+// Step 3: batched pruned BFS + cleanup + append, then step 4.
+int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, const uint8_t *inX,
+                 uint32_t bmax, uint32_t block, cudaStream_t s) {
+    const uint32_t n = ix->n;
+    LabelStore st;
+    st.n = n;
+    DevMem m_off, m_len, m_cap, m_pool, m_ctr;
+    PLL_CHECK(m_off.alloc((size_t)n * 8));
+    PLL_CHECK(m_len.alloc((size_t)n * 4));
+    PLL_CHECK(m_cap.alloc((size_t)n * 4));
+    PLL_CHECK(m_ctr.alloc(sizeof(Counters)));
+    PLL_TRY(cudaMemsetAsync(m_off.p, 0, (size_t)n * 8, s));
+    PLL_TRY(cudaMemsetAsync(m_len.p, 0, (size_t)n * 4, s));
+    PLL_TRY(cudaMemsetAsync(m_cap.p, 0, (size_t)n * 4, s));
+    PLL_TRY(cudaMemsetAsync(m_ctr.p, 0, sizeof(Counters), s));
+    Counters *d_ctr = m_ctr.as<Counters>();
+    st.off = m_off.as<uint64_t>();
+    st.len = m_len.as<uint32_t>();
+    st.cap = m_cap.as<uint32_t>();
+    st.pool_cap = std::max<uint64_t>((uint64_t)n * 16, 1ull << 22);
+    PLL_CHECK(m_pool.alloc(st.pool_cap * 4));
+    st.pool = m_pool.as<uint32_t>();
+    m_pool.release();  // owned through st.pool from here on (regrow swaps it)
+    st.pool_top = &d_ctr->pool_top;
+    struct PoolGuard {
+        LabelStore *st;
+        ~PoolGuard() { if (st->pool) cudaFree(st->pool); }
+    } pool_guard{&st};
+
+    // per-team BFS queues, visited bitmap, tuple buffers
+    int grid = 0;
+    PLL_CHECK(pruned_max_grid(block, &grid));
+    const uint64_t queue_budget = 6ull << 30;  // bytes
+    if ((uint64_t)grid * n * 4 > queue_budget) grid = (int)std::max<uint64_t>(1, queue_budget / ((uint64_t)n * 4));
+    DevMem m_q, m_vis, m_buf, m_sorted, m_keep, m_temp;
+    PLL_CHECK(m_q.alloc((size_t)grid * n * 4));
+    const uint32_t wmax = (bmax + 31) / 32;
+    PLL_CHECK(m_vis.alloc((size_t)n * wmax * 4));
+    uint64_t out_cap = std::max<uint64_t>((uint64_t)n * 2, 1ull << 20);
+    size_t temp_bytes = 0;
+    const int end_bit = 32 + std::max(1, bit_length(n - 1));
+    auto alloc_buffers = [&]() -> int {
+        PLL_CHECK(m_buf.alloc(out_cap * 8));
+        PLL_CHECK(m_sorted.alloc(out_cap * 8));
+        PLL_CHECK(m_keep.alloc(out_cap));
+        size_t a = 0, b = 0;
+        PLL_CHECK(labels_sort_tuples(nullptr, nullptr, out_cap, end_bit, nullptr, &a, s));
+        PLL_CHECK(labels_compact(nullptr, nullptr, out_cap, nullptr, nullptr, nullptr, &b, s));
+        temp_bytes = std::max(a, b);
+        PLL_CHECK(m_temp.alloc(temp_bytes));
+        return PLL_OK;
+    };
+    PLL_CHECK(alloc_buffers());
+
+    Counters h{};
+    uint64_t total = 0, pre = 0, visited = 0, batches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    PLL_TRY(cudaEventCreate(&ev0));
+    PLL_TRY(cudaEventCreate(&ev1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev_guard{ev0, ev1};
+    uint32_t k0 = 0, B = std::min<uint32_t>(32, bmax);
+    while (k0 < n) {
+        const uint32_t k1 = (uint32_t)std::min<uint64_t>(n, (uint64_t)k0 + B);
+        const uint32_t W = (k1 - k0 + 31) / 32;
+        PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)n * W * 4, s));
+        PLL_TRY(cudaMemsetAsync(&d_ctr->out_cnt, 0, 24, s));  // out_cnt, nkept, visit_cnt
+        PLL_TRY(cudaMemcpyAsync(&d_ctr->next_root, &k0, 4, cudaMemcpyHostToDevice, s));
+        PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
+        PrunedBatch b{};
+        b.n = n; b.t = ix->t;
+        b.roff = roff; b.rcol = rcol;
+        b.bp_d = ix->d_bp_d; b.bp_m = ix->d_bp_m; b.inX = inX;
+        b.lab_off = st.off; b.lab_len = st.len; b.pool = st.pool;
+        b.k0 = k0; b.k1 = k1;
+        b.next_root = &d_ctr->next_root;
+        b.visited = m_vis.as<uint32_t>(); b.W = W;
+        b.queues = m_q.as<uint32_t>();
+        b.out = m_buf.as<uint64_t>(); b.out_cnt = &d_ctr->out_cnt; b.out_cap = out_cap;
+        b.visit_cnt = &d_ctr->visit_cnt;
+        b.work = d_ctr->work;
+        b.err = &d_ctr->err;
+        const int g = (int)std::min<uint64_t>(grid, k1 - k0);
+        PLL_TRY(cudaEventRecord(ev0, s));
+        PLL_CHECK(pruned_launch(b, g, block, s));
+        PLL_TRY(cudaEventRecord(ev1, s));
+        PLL_TRY(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        PLL_TRY(cudaStreamSynchronize(s));
+        {
+            float ms = 0;
+            PLL_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+            ix->stats.ms_pruned_kernel += ms;
+            ix->stats.pruned_launches += 1;
+            ix->stats.launches += 1;
+        }
+        if (h.err & ERR_DEPTH) return PLL_E_RANGE;
+        if (h.err & ERR_BUF) {  // more tuples than buffer: grow and redo the batch
+            out_cap = std::max<uint64_t>(out_cap * 2, h.out_cnt + h.out_cnt / 4);
+            PLL_CHECK(alloc_buffers());
+            continue;
+        }
+        const uint64_t P = h.out_cnt;
+        visited += h.visit_cnt;
+        pre += P;
+        if (P > 0) {
+            // worst-case pool growth of one append: 2 x (entries + new) + 8 per run
+            const uint64_t need = h.pool_top + 2 * (total + P) + 8 * P;
+            if (need > st.pool_cap) {
+                uint64_t nc = std::max<uint64_t>(st.pool_cap * 2, 3 * (total + P) + 8 * P);
+                PLL_CHECK(labels_regrow(st, nc, s));
+            }
+            size_t tb = temp_bytes;
+            PLL_CHECK(labels_sort_tuples(m_buf.as<uint64_t>(), m_sorted.as<uint64_t>(), P, end_bit,
+                                         m_temp.p, &tb, s));
+            PLL_CHECK(labels_cleanup(m_sorted.as<uint64_t>(), P, m_keep.as<uint8_t>(), s));
+            tb = temp_bytes;
+            PLL_CHECK(labels_compact(m_sorted.as<uint64_t>(), m_keep.as<uint8_t>(), P,
+                                     m_buf.as<uint64_t>(), &d_ctr->nkept, m_temp.p, &tb, s));
+            PLL_CHECK(labels_append(st, m_buf.as<uint64_t>(), &d_ctr->nkept, P, &d_ctr->err, s));
+            ix->stats.launches += 2;   // cleanup, append
+            ix->stats.cub_calls += 2;  // sort, select
+            PLL_TRY(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+            PLL_TRY(cudaStreamSynchronize(s));
+            if (h.err & ERR_POOL) return PLL_E_NOMEM;
+            total += h.nkept;
+        }
+        ++batches;
+        k0 = k1;
+        B = std::min<uint32_t>(B * 2, bmax);
+    }
+    ix->stats.pruned_scanned = h.work[0];
+    ix->stats.pruned_masks = h.work[1];
+    ix->stats.pruned_expanded = h.work[2];
+    ix->stats.label_entries = total;
+    ix->stats.pre_cleanup = pre;
+    ix->stats.visited = visited;
+    ix->stats.batches = batches;
+    ix->entries = total;
+
+    // step 4: compact CSR
+    PLL_TRY(cudaMalloc(&ix->d_lab_off, ((size_t)n + 1) * 8));
+    PLL_TRY(cudaMalloc(&ix->d_lab, std::max<uint64_t>(total, 1) * 4));
+    size_t ftb = 0;
+    PLL_CHECK(labels_finalize(st, total, ix->d_lab_off, ix->d_lab, nullptr, &ftb, s));
+    DevMem ftemp;
+    PLL_CHECK(ftemp.alloc(ftb));
+    Timer tf(s);
+    tf.start();
+    PLL_CHECK(labels_finalize(st, total, ix->d_lab_off, ix->d_lab, ftemp.p, &ftb, s));
+    ix->stats.ms_finalize = tf.stop_ms();
+    ix->stats.launches += 3;   // widen, set, gather
+    ix->stats.cub_calls += 1;  // scan
+    return PLL_OK;
+}
+
+int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t nnz,
+                 const uint32_t *order, const pll_build_opts *opts, cudaStream_t s,
+                 pll_index **out) {
+    pll_build_opts o{};
+    if (opts) o = *opts;
+    if (!out) return PLL_E_INVAL;
+    *out = nullptr;
+    if (o.reserved != 0 || o.flags != 0) return PLL_E_INVAL;
+    if (o.t > PLL_MAX_T) return PLL_E_RANGE;
+    if (n > MAX_N || nnz >= 0xffffffffull) return PLL_E_RANGE;
+    if (n > 0 && !off) return PLL_E_INVAL;
+    if (nnz > 0 && !col) return PLL_E_INVAL;
+    if (n == 0 && nnz != 0) return PLL_E_INVAL;
+    uint32_t block = o.block ? o.block : 256;
+    if (block != 128 && block != 256 && block != 512) return PLL_E_INVAL;
+    uint32_t bmax = o.root_batch ? o.root_batch : 1024;
+    if (bmax > (1u << 16)) bmax = 1u << 16;
+
+    pll_index *ix = new (std::nothrow) pll_index();
+    if (!ix) return PLL_E_NOMEM;
+    struct Guard {
+        pll_index *ix;
+        ~Guard() { free_index(ix); }
+    } guard{ix};
+    PLL_TRY(cudaGetDevice(&ix->device));
+    ix->n = n;
+    ix->t = o.t;
+    ix->nnz = nnz;
+    ix->stats.n = n;
+    ix->stats.t = o.t;
+    ix->stats.nnz = nnz;
+    Timer tm(s);
+
+    // ---- 1. checks, order, relabel
+    tm.start();
+    DevMem m_err;
+    PLL_CHECK(m_err.alloc(4));
+    uint32_t *d_err = m_err.as<uint32_t>();
+    uint32_t h_err = 0;
+    PLL_TRY(cudaMemsetAsync(d_err, 0, 4, s));
+    Graph g;
+    g.n = n; g.nnz = nnz; g.off = off; g.col = col;
+    PLL_CHECK(prep_validate_csr(g, d_err, s));
+    PLL_CHECK(read_err(d_err, s, &h_err));
+    if (h_err) return PLL_E_INVAL;
+    PLL_TRY(cudaMalloc(&ix->d_order, std::max<size_t>((size_t)n * 4, 4)));
+    PLL_TRY(cudaMalloc(&ix->d_inv, std::max<size_t>((size_t)n * 4, 4)));
+    if (order) {
+        if (n) PLL_TRY(cudaMemcpyAsync(ix->d_order, order, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        PLL_CHECK(prep_check_order(g, ix->d_order, d_err, s));
+        PLL_CHECK(read_err(d_err, s, &h_err));
+        if (h_err) return PLL_E_ORDER;
+    } else {
+        PLL_CHECK(prep_degree_order(g, ix->d_order, s));
+    }
+    DevMem m_roff, m_rcol, m_inX;
+    PLL_CHECK(m_roff.alloc(((size_t)n + 1) * 4));
+    PLL_CHECK(m_rcol.alloc(std::max<uint64_t>(nnz, 1) * 4));
+    PLL_CHECK(prep_relabel(g, ix->d_order, ix->d_inv, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), s));
+    PLL_CHECK(m_inX.alloc(std::max<size_t>(n, 1)));
+    PLL_TRY(cudaMemsetAsync(m_inX.p, 0, std::max<size_t>(n, 1), s));
+    const uint32_t t = o.t;
+    PLL_TRY(cudaMalloc(&ix->d_bp_root, std::max<size_t>(t, 1) * 4));
+    PLL_TRY(cudaMalloc(&ix->d_bp_cnt, std::max<size_t>(t, 1) * 4));
+    PLL_TRY(cudaMalloc(&ix->d_bp_S, std::max<size_t>((size_t)t * BPW, 1) * 4));
+    PLL_TRY(cudaMemsetAsync(ix->d_bp_S, 0xff, std::max<size_t>((size_t)t * BPW, 1) * 4, s));
+    PLL_CHECK(prep_select_bp_roots(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(),
+                                   m_inX.as<uint8_t>(), ix->d_bp_root, ix->d_bp_cnt, ix->d_bp_S, s));
+    ix->stats.ms_prep = tm.stop_ms();
+
+    // ---- 2. bit-parallel labels
+    tm.start();
+    const size_t nt = (size_t)n * t;
+    PLL_TRY(cudaMalloc(&ix->d_bp_d, std::max<size_t>(nt, 1)));
+    PLL_TRY(cudaMalloc(&ix->d_bp_m, std::max<size_t>(nt, 1) * 16));
+    PLL_CHECK(bp_run(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), ix->d_bp_root,
+                     ix->d_bp_cnt, ix->d_bp_S, ix->d_bp_d, ix->d_bp_m, d_err, s));
+    PLL_CHECK(read_err(d_err, s, &h_err));
+    if (h_err) return err_to_status(h_err);
+    ix->stats.ms_bp = tm.stop_ms();
+
+    // ---- 3 + 4. pruned labels
+    tm.start();
+    PLL_CHECK(pruned_stage(ix, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), m_inX.as<uint8_t>(),
+                           bmax, block, s));
+    ix->stats.ms_pruned = tm.stop_ms();
+
+    PLL_TRY(cudaMalloc(&ix->d_qerr, 16));
+    PLL_TRY(cudaMemsetAsync(ix->d_qerr, 0, 16, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    ix->stats.index_bytes = (uint64_t)n * 8 + nt * 17 + ((uint64_t)n + 1) * 8 + ix->entries * 4 +
+                            (uint64_t)t * (BPW + 2) * 4;
+    *out = ix;
+    guard.ix = nullptr;
+    return PLL_OK;
+}
+
+// temporary device copy of a host array, stream ordered
+struct AsyncBuf {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit AsyncBuf(cudaStream_t st) : s(st) {}
+    ~AsyncBuf() { if (p) cudaFreeAsync(p, s); }
+    int alloc(size_t b) {
+        cudaError_t e = cudaMallocAsync(&p, b ? b : 16, s);
+        if (e != cudaSuccess) { p = nullptr; (void)cudaGetLastError(); return PLL_E_NOMEM; }
+        return PLL_OK;
+    }
+};
+
+int query_status(const pll_index *ix, cudaStream_t s) {
+    unsigned long long h[2] = {0, 0};
+    PLL_TRY(cudaMemcpyAsync(h, ix->d_qerr, 16, cudaMemcpyDeviceToHost, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    if (h[0] == 0 && h[1] == 0) return PLL_OK;
+    PLL_TRY(cudaMemsetAsync(ix->d_qerr, 0, 16, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    return h[1] ? PLL_E_INVAL : PLL_E_RANGE;
+}
+
+}  // namespace
+}  // namespace pll
+
+using namespace pll;
+
+extern "C" {
+
+PLL_API const char *pll_status_str(int status) {
+    switch (status) {
+        case PLL_OK: return "ok";
+        case PLL_E_INVAL: return "invalid argument or malformed graph";
+        case PLL_E_ORDER: return "order is not a permutation of 0..n-1";
+        case PLL_E_RANGE: return "size or distance out of range";
+        case PLL_E_NOMEM: return "out of memory";
+        case PLL_E_TIMEOUT: return "bounded device wait expired";
+        case PLL_E_CUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+PLL_API int pll_build(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                      const uint32_t *order, const pll_build_opts *opts, void *stream,
+                      pll_index **out) {
+    return build_device(offsets, cols, n, nnz, order, opts, (cudaStream_t)stream, out);
+}
+
+PLL_API int pll_build_host(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
+                           uint64_t nnz, const uint32_t *order, const pll_build_opts *opts,
+                           void *stream, pll_index **out) {
+    if (!out) return PLL_E_INVAL;
+    *out = nullptr;
+    if (n > MAX_N || nnz >= 0xffffffffull) return PLL_E_RANGE;
+    if ((n > 0 && !offsets) || (nnz > 0 && !cols)) return PLL_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = PLL_OK;
+    {
+        AsyncBuf doff(s), dcol(s), dord(s);
+        PLL_CHECK(doff.alloc(((size_t)n + 1) * 4));
+        PLL_CHECK(dcol.alloc(std::max<uint64_t>(nnz, 1) * 4));
+        if (offsets)
+            PLL_TRY(cudaMemcpyAsync(doff.p, offsets, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s));
+        else
+            PLL_TRY(cudaMemsetAsync(doff.p, 0, 4, s));
+        if (nnz) PLL_TRY(cudaMemcpyAsync(dcol.p, cols, nnz * 4, cudaMemcpyHostToDevice, s));
+        if (order) {
+            PLL_CHECK(dord.alloc(std::max<size_t>((size_t)n * 4, 4)));
+            if (n) PLL_TRY(cudaMemcpyAsync(dord.p, order, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        }
+        st = build_device((const uint32_t *)doff.p, (const uint32_t *)dcol.p, n, nnz,
+                          order ? (const uint32_t *)dord.p : nullptr, opts, s, out);
+    }
+    if (st == PLL_OK) PLL_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
+PLL_API int pll_query_async(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
+                            uint64_t q, uint8_t *out, void *stream) {
+    if (!idx) return PLL_E_INVAL;
+    if (q == 0) return PLL_OK;
+    if (!src || !dst || !out) return PLL_E_INVAL;
+    return query_launch(idx, src, dst, q, out, (cudaStream_t)stream);
+}
+
+PLL_API int pll_query_errors(const pll_index *idx, void *stream, uint64_t *count) {
+    if (!idx || !count) return PLL_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long h[2] = {0, 0};
+    PLL_TRY(cudaMemcpyAsync(h, idx->d_qerr, 16, cudaMemcpyDeviceToHost, s));
+    PLL_TRY(cudaMemsetAsync(idx->d_qerr, 0, 16, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    *count = h[0] + h[1];
+    return PLL_OK;
+}
+
+PLL_API int pll_query(const pll_index *idx, const uint32_t *src, const uint32_t *dst, uint64_t q,
+                      uint8_t *out, void *stream) {
+    if (!idx) return PLL_E_INVAL;
+    if (q == 0) return PLL_OK;
+    if (!src || !dst || !out) return PLL_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PLL_CHECK(query_launch(idx, src, dst, q, out, s));
+    return query_status(idx, s);
+}
+
+PLL_API int pll_query_host(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
+                           uint64_t q, uint8_t *out, void *stream) {
+    if (!idx) return PLL_E_INVAL;
+    if (q == 0) return PLL_OK;
+    if (!src || !dst || !out) return PLL_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st;
+    {
+        AsyncBuf ds(s), dd(s), dout(s);
+        PLL_CHECK(ds.alloc(q * 4));
+        PLL_CHECK(dd.alloc(q * 4));
+        PLL_CHECK(dout.alloc(q));
+        PLL_TRY(cudaMemcpyAsync(ds.p, src, q * 4, cudaMemcpyHostToDevice, s));
+        PLL_TRY(cudaMemcpyAsync(dd.p, dst, q * 4, cudaMemcpyHostToDevice, s));
+        PLL_CHECK(query_launch(idx, (const uint32_t *)ds.p, (const uint32_t *)dd.p, q,
+                               (uint8_t *)dout.p, s));
+        PLL_TRY(cudaMemcpyAsync(out, dout.p, q, cudaMemcpyDeviceToHost, s));
+        st = query_status(idx, s);
+    }
+    PLL_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
+PLL_API int pll_label_entries(const pll_index *idx, uint64_t *total) {
+    if (!idx || !total) return PLL_E_INVAL;
+    *total = idx->entries;
+    return PLL_OK;
+}
+
+PLL_API int pll_export_labels(const pll_index *idx, uint64_t *offsets, uint32_t *hubs,
+                              uint8_t *dists) {
+    if (!idx || !offsets || (idx->entries && (!hubs || !dists))) return PLL_E_INVAL;
+    const uint32_t n = idx->n;
+    std::vector<uint64_t> off((size_t)n + 1);
+    std::vector<uint32_t> lab(idx->entries), inv(n);
+    PLL_TRY(cudaMemcpy(off.data(), idx->d_lab_off, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost));
+    if (idx->entries)
+        PLL_TRY(cudaMemcpy(lab.data(), idx->d_lab, idx->entries * 4, cudaMemcpyDeviceToHost));
+    if (n) PLL_TRY(cudaMemcpy(inv.data(), idx->d_inv, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    uint64_t p = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+        offsets[v] = p;
+        const uint32_t r = inv[v];
+        for (uint64_t j = off[r]; j < off[(size_t)r + 1]; ++j, ++p) {
+            hubs[p] = entry_hub(lab[j]);
+            dists[p] = (uint8_t)entry_dist(lab[j]);
+        }
+    }
+    offsets[n] = p;
+    return PLL_OK;
+}
+
+PLL_API int pll_export_bp(const pll_index *idx, uint8_t *d, uint64_t *m1, uint64_t *m0) {
+    if (!idx) return PLL_E_INVAL;
+    const uint32_t n = idx->n, t = idx->t;
+    if (t == 0 || n == 0) return PLL_OK;
+    if (!d || !m1 || !m0) return PLL_E_INVAL;
+    const size_t nt = (size_t)n * t;
+    std::vector<uint8_t> hd(nt);
+    std::vector<uint64_t> hm(2 * nt);
+    std::vector<uint32_t> inv(n);
+    PLL_TRY(cudaMemcpy(hd.data(), idx->d_bp_d, nt, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hm.data(), idx->d_bp_m, nt * 16, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(inv.data(), idx->d_inv, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    for (uint32_t v = 0; v < n; ++v) {
+        const size_t r = (size_t)inv[v] * t, o = (size_t)v * t;
+        for (uint32_t i = 0; i < t; ++i) {
+            d[o + i] = hd[r + i];
+            m1[o + i] = hm[2 * (r + i)];
+            m0[o + i] = hm[2 * (r + i) + 1];
+        }
+    }
+    return PLL_OK;
+}
+
+PLL_API int pll_export_bp_roots(const pll_index *idx, uint32_t *roots, uint32_t *cnt, uint32_t *S) {
+    if (!idx) return PLL_E_INVAL;
+    const uint32_t t = idx->t, n = idx->n;
+    if (t == 0) return PLL_OK;
+    if (!roots || !cnt || !S) return PLL_E_INVAL;
+    std::vector<uint32_t> order(n);
+    std::vector<uint32_t> hr(t), hc(t), hs((size_t)t * BPW);
+    if (n) PLL_TRY(cudaMemcpy(order.data(), idx->d_order, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hr.data(), idx->d_bp_root, (size_t)t * 4, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hc.data(), idx->d_bp_cnt, (size_t)t * 4, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hs.data(), idx->d_bp_S, (size_t)t * BPW * 4, cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < t; ++i) {
+        roots[i] = hr[i] == NONE ? NONE : order[hr[i]];
+        cnt[i] = hc[i];
+        for (uint32_t j = 0; j < BPW; ++j) {
+            const uint32_t r = hs[(size_t)i * BPW + j];
+            S[(size_t)i * BPW + j] = (j < hc[i] && r != NONE) ? order[r] : NONE;
+        }
+    }
+    return PLL_OK;
+}
+
+PLL_API int pll_export_order(const pll_index *idx, uint32_t *order) {
+    if (!idx || (idx->n && !order)) return PLL_E_INVAL;
+    if (idx->n) PLL_TRY(cudaMemcpy(order, idx->d_order, (size_t)idx->n * 4, cudaMemcpyDeviceToHost));
+    return PLL_OK;
+}
+
+PLL_API int pll_get_stats(const pll_index *idx, pll_stats *out) {
+    if (!idx || !out) return PLL_E_INVAL;
+    *out = idx->stats;
+    return PLL_OK;
+}
+
+PLL_API void pll_free(pll_index *idx) { free_index(idx); }
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// pll_internal.cuh -- shared declarations of libpll.so (never installed).
+//
+// Everything inside the library works in RANK SPACE: vertex ids are replaced
+// by their rank in the vertex order (the paper stores hub ranks instead of
+// vertex ids so labels come out sorted, Sec. 4.5.1 "Sorting Labels"; here the
+// whole graph is relabelled once so that hub rank == vertex id). The caller's
+// ids are translated only at the ABI boundary (queries, exports).
+//
+// Device layouts (all in rank space, n vertices, t bit-parallel roots):
+//   roff[n+1], rcol[nnz]      CSR, neighbour lists ascending by rank
+//   bp_d[n*t]                 d_G(r_i, v), 255 = unreachable (Sec. 5.1)
+//   bp_m[2*(n*t)]             interleaved (S^{-1}, S^0) 64-bit sets per (v, i)
+//   label entry (uint32)      (hub rank << 8) | distance, hub rank < 2^24
+//   labels during the build   per-vertex growable arrays in one pool
+//   labels after the build    CSR: lab_off[n+1] (uint64), lab[...] (uint32)
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pll.h"
+
+namespace pll {
+
+constexpr uint8_t INF8 = 255;
+constexpr uint32_t NONE = 0xffffffffu;
+constexpr int BPW = 64;                  // bits per bit-parallel word (b, Sec. 5)
+constexpr uint32_t MAX_N = (1u << 24) - 1;  // hub ranks are packed into 24 bits
+
+// error bits raised by kernels into a device word
+enum : uint32_t {
+    ERR_CSR = 1u << 0,     // malformed CSR
+    ERR_ORDER = 1u << 1,   // order is not a permutation
+    ERR_DEPTH = 1u << 2,   // BFS depth reached 255
+    ERR_BUF = 1u << 3,     // tuple buffer overflow (batch must be split)
+    ERR_POOL = 1u << 4,    // label pool overflow
+};
+
+__host__ __device__ inline uint32_t pack_entry(uint32_t hub, uint32_t d) { return (hub << 8) | d; }
+__host__ __device__ inline uint32_t entry_hub(uint32_t e) { return e >> 8; }
+__host__ __device__ inline uint32_t entry_dist(uint32_t e) { return e & 0xffu; }
+
+// A pre-cleanup tuple of a root batch: (vertex u, hub k, distance).
+// Sorting the 64-bit key orders tuples by vertex, then hub.
+__host__ __device__ inline uint64_t pack_tuple(uint32_t u, uint32_t k, uint32_t d) {
+    return ((uint64_t)u << 32) | pack_entry(k, d);
+}
+
+}  // namespace pll
+
+// The opaque index of the C ABI.
+struct pll_index {
+    int device = 0;
+    uint32_t n = 0, t = 0;
+    uint64_t nnz = 0;
+    uint32_t *d_order = nullptr;   // rank -> caller vertex id
+    uint32_t *d_inv = nullptr;     // caller vertex id -> rank
+    uint8_t *d_bp_d = nullptr;     // [n][t]
+    uint64_t *d_bp_m = nullptr;    // [n][t][2]
+    uint32_t *d_bp_root = nullptr; // [t] ranks (NONE = empty slot)
+    uint32_t *d_bp_cnt = nullptr;  // [t]
+    uint32_t *d_bp_S = nullptr;    // [t][64] ranks
+    uint64_t *d_lab_off = nullptr; // [n+1]
+    uint32_t *d_lab = nullptr;     // packed entries
+    uint64_t entries = 0;
+    unsigned long long *d_qerr = nullptr;  // query error counter
+    pll_stats stats{};
+};
+
+namespace pll {
+
+// ---- host helpers (pll_abi.cu) ----
+int cuda_status(cudaError_t e);  // maps a CUDA error to a pll_status
+
+#define PLL_TRY(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return ::pll::cuda_status(_e); \
+    } while (0)
+
+#define PLL_CHECK(st)              \
+    do {                           \
+        int _s = (st);             \
+        if (_s != PLL_OK) return _s; \
+    } while (0)
+
+// Device allocation that frees itself; release() hands ownership out.
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    ~DevMem() { reset(); }
+    int alloc(size_t b) {
+        reset();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) { p = nullptr; (void)cudaGetLastError(); return PLL_E_NOMEM; }
+        bytes = b;
+        return PLL_OK;
+    }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    void *release() { void *q = p; p = nullptr; bytes = 0; return q; }
+};
+
+// ---- launchers (one translation unit each) ----
+struct Graph {
+    uint32_t n = 0;
+    uint64_t nnz = 0;
+    const uint32_t *off = nullptr;  // caller space
+    const uint32_t *col = nullptr;
+};
+
+// k_prep.cu
+int prep_validate_csr(const Graph &g, uint32_t *d_err, cudaStream_t s);
+int prep_degree_order(const Graph &g, uint32_t *d_order, cudaStream_t s);
+int prep_check_order(const Graph &g, const uint32_t *d_order, uint32_t *d_err, cudaStream_t s);
+int prep_relabel(const Graph &g, const uint32_t *d_order, uint32_t *d_inv, uint32_t *d_roff,
+                 uint32_t *d_rcol, cudaStream_t s);
+int prep_select_bp_roots(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
+                         uint8_t *d_inX, uint32_t *d_root, uint32_t *d_cnt, uint32_t *d_S,
+                         cudaStream_t s);
+
+// k_bp.cu
+int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
+           const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S, uint8_t *d_bp_d,
+           uint64_t *d_bp_m, uint32_t *d_err, cudaStream_t s);
+
+// k_pruned.cu
+struct PrunedBatch {
+    uint32_t n, t;
+    const uint32_t *roff, *rcol;
+    const uint8_t *bp_d;
+    const uint64_t *bp_m;
+    const uint8_t *inX;
+    const uint64_t *lab_off;   // per-vertex start in pool
+    const uint32_t *lab_len;   // per-vertex length (entries with hub < k0)
+    const uint32_t *pool;
+    uint32_t k0, k1;           // roots of this batch: ranks [k0, k1)
+    uint32_t *next_root;       // work counter, starts at k0
+    uint32_t *visited;         // [n][W] bitmap, one bit per batch root
+    uint32_t W;
+    uint32_t *queues;          // [grid][n]
+    uint64_t *out;             // pre-cleanup tuples
+    unsigned long long *out_cnt;
+    uint64_t out_cap;
+    unsigned long long *visit_cnt;
+    unsigned long long *work;  // [0] label entries scanned, [1] mask pairs, [2] arcs expanded
+    uint32_t *err;
+};
+int pruned_max_grid(uint32_t block, int *grid);
+int pruned_launch(const PrunedBatch &b, int grid, uint32_t block, cudaStream_t s);
+
+// k_labels.cu
+struct LabelStore {
+    uint32_t n = 0;
+    uint64_t *off = nullptr;   // [n]
+    uint32_t *len = nullptr;   // [n]
+    uint32_t *cap = nullptr;   // [n]
+    uint32_t *pool = nullptr;
+    uint64_t pool_cap = 0;
+    unsigned long long *pool_top = nullptr;
+};
+int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int end_bit,
+                       void *d_temp, size_t *temp_bytes, cudaStream_t s);
+int labels_cleanup(const uint64_t *d_sorted, uint64_t count, uint8_t *d_keep, cudaStream_t s);
+int labels_compact(const uint64_t *d_in, const uint8_t *d_keep, uint64_t count, uint64_t *d_out,
+                   unsigned long long *d_nout, void *d_temp, size_t *temp_bytes, cudaStream_t s);
+int labels_append(const LabelStore &st, const uint64_t *d_kept,
+                  const unsigned long long *d_nkept, uint64_t max_count, uint32_t *d_err,
+                  cudaStream_t s);
+int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s);
+int labels_finalize(const LabelStore &st, uint64_t total, uint64_t *d_off, uint32_t *d_lab,
+                    void *d_temp, size_t *temp_bytes, cudaStream_t s);
+int scan_u32_to_u64(const uint32_t *d_in, uint64_t *d_out, uint32_t n, void *d_temp,
+                    size_t *temp_bytes, cudaStream_t s);
+
+// k_query.cu
+int query_launch(const pll_index *ix, const uint32_t *d_src, const uint32_t *d_dst, uint64_t q,
+                 uint8_t *d_out, cudaStream_t s);
+
+}  // namespace pll

@@ -1,0 +1,264 @@
+"""ctypes binding of libpll.so (include/pll.h) -- argument marshalling only.
+
+Every step of the index build and of the queries runs in the library's CUDA
+kernels. Device arguments are torch CUDA tensors (their data pointers and
+the current CUDA stream are passed through); host arguments are numpy arrays
+and go to the ``*_host`` entry points, which copy inside the call. There is
+no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+PLL_OK, PLL_E_INVAL, PLL_E_ORDER, PLL_E_RANGE, PLL_E_NOMEM, PLL_E_TIMEOUT, PLL_E_CUDA = range(7)
+PLL_MAX_T = 64
+NONE = 0xFFFFFFFF
+
+SYMBOLS = [
+    "pll_build", "pll_build_host", "pll_query", "pll_query_async", "pll_query_errors",
+    "pll_query_host", "pll_label_entries", "pll_export_labels", "pll_export_bp",
+    "pll_export_bp_roots", "pll_export_order", "pll_get_stats", "pll_free", "pll_status_str",
+]
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("t", C.c_uint32), ("root_batch", C.c_uint32), ("block", C.c_uint32),
+                ("flags", C.c_uint32), ("reserved", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("t", C.c_uint32), ("nnz", C.c_uint64),
+                ("label_entries", C.c_uint64), ("pre_cleanup", C.c_uint64),
+                ("visited", C.c_uint64), ("batches", C.c_uint64), ("index_bytes", C.c_uint64),
+                ("ms_prep", C.c_double), ("ms_bp", C.c_double), ("ms_pruned", C.c_double),
+                ("ms_finalize", C.c_double), ("ms_pruned_kernel", C.c_double),
+                ("pruned_launches", C.c_uint64), ("pruned_scanned", C.c_uint64),
+                ("pruned_masks", C.c_uint64), ("pruned_expanded", C.c_uint64),
+                ("launches", C.c_uint64), ("cub_calls", C.c_uint64)]
+
+
+class PLLError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_str(code)} (status {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return str(_build.OUT / "libpll.so")
+
+
+def load(build_if_missing: bool = True):
+    """Load libpll.so (building it in-tree with nvcc when absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if build_if_missing:
+        path = _build.build_pll()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpll.so not found at {path}; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+    pp = C.POINTER(C.c_void_p)
+    for name in ("pll_build", "pll_build_host"):
+        f = getattr(lib, name)
+        f.restype = i32
+        f.argtypes = [vp, vp, u32, u64, vp, C.POINTER(BuildOpts), vp, pp]
+    for name in ("pll_query", "pll_query_async", "pll_query_host"):
+        f = getattr(lib, name)
+        f.restype = i32
+        f.argtypes = [vp, vp, vp, u64, vp, vp]
+    lib.pll_query_errors.restype = i32
+    lib.pll_query_errors.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
+    lib.pll_label_entries.restype = i32
+    lib.pll_label_entries.argtypes = [vp, C.POINTER(C.c_uint64)]
+    lib.pll_export_labels.restype = i32
+    lib.pll_export_labels.argtypes = [vp, vp, vp, vp]
+    lib.pll_export_bp.restype = i32
+    lib.pll_export_bp.argtypes = [vp, vp, vp, vp]
+    lib.pll_export_bp_roots.restype = i32
+    lib.pll_export_bp_roots.argtypes = [vp, vp, vp, vp]
+    lib.pll_export_order.restype = i32
+    lib.pll_export_order.argtypes = [vp, vp]
+    lib.pll_get_stats.restype = i32
+    lib.pll_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    lib.pll_free.restype = None
+    lib.pll_free.argtypes = [vp]
+    lib.pll_status_str.restype = C.c_char_p
+    lib.pll_status_str.argtypes = [i32]
+    _lib = lib
+    return lib
+
+
+def status_str(code: int) -> str:
+    return load().pll_status_str(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != PLL_OK:
+        raise PLLError(code, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(x):
+    assert x.is_cuda and x.is_contiguous(), "device arguments must be contiguous CUDA tensors"
+    return x.data_ptr()
+
+
+def _hptr(a, dtype):
+    a = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    return a, a.ctypes.data
+
+
+@dataclass
+class Labels:
+    offsets: np.ndarray  # uint64 [n + 1], by vertex id
+    hubs: np.ndarray     # uint32 hub ranks
+    dists: np.ndarray    # uint8
+
+
+class Index:
+    """A PLL index resident on the current CUDA device."""
+
+    def __init__(self, handle: int, n: int, t: int):
+        self._h = handle
+        self.n = n
+        self.t = t
+
+    # ------------------------------------------------------------- build
+    @classmethod
+    def build(cls, offsets, cols, t: int = 0, order=None, root_batch: int = 0, block: int = 0,
+              stream=None) -> "Index":
+        """pll_build (CUDA tensors) or pll_build_host (numpy arrays)."""
+        lib = load()
+        opts = BuildOpts(t, root_batch, block, 0, 0)
+        out = C.c_void_p()
+        n = int(offsets.shape[0]) - 1
+        nnz = int(cols.shape[0])
+        if _is_torch(offsets):
+            import torch
+            assert offsets.dtype == torch.int32 or offsets.dtype == torch.uint32
+            optr = _dptr(order) if order is not None else None
+            st = lib.pll_build(_dptr(offsets), _dptr(cols) if nnz else None, n, nnz, optr,
+                               C.byref(opts), _stream_handle(stream), C.byref(out))
+        else:
+            off, op = _hptr(offsets, np.uint32)
+            col, cp = _hptr(cols, np.uint32)
+            ordp = None
+            if order is not None:
+                order_a, ordp = _hptr(order, np.uint32)
+            st = lib.pll_build_host(op, cp if nnz else None, n, nnz, ordp, C.byref(opts),
+                                    _stream_handle(stream) if stream is not None else None,
+                                    C.byref(out))
+        _check(st, "pll_build")
+        return cls(out.value, n, t)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pll_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- query
+    def query(self, src, dst, out=None, stream=None):
+        """Distances for pairs (src[i], dst[i]); CUDA tensors in -> CUDA uint8
+        tensor out (synchronous), numpy in -> numpy out (pll_query_host)."""
+        lib = load()
+        q = int(src.shape[0])
+        if _is_torch(src):
+            import torch
+            if out is None:
+                out = torch.empty(q, dtype=torch.uint8, device=src.device)
+            if q:
+                _check(lib.pll_query(self._h, _dptr(src), _dptr(dst), q, _dptr(out),
+                                     _stream_handle(stream)), "pll_query")
+            return out
+        s, sp = _hptr(src, np.uint32)
+        d, dp = _hptr(dst, np.uint32)
+        res = np.empty(max(q, 1), dtype=np.uint8)
+        if q:
+            _check(lib.pll_query_host(self._h, sp, dp, q, res.ctypes.data,
+                                      _stream_handle(stream) if stream is not None else None),
+                   "pll_query_host")
+        return res[:q]
+
+    def query_async(self, src, dst, out, stream=None):
+        q = int(src.shape[0])
+        if q:
+            _check(load().pll_query_async(self._h, _dptr(src), _dptr(dst), q, _dptr(out),
+                                          _stream_handle(stream)), "pll_query_async")
+        return out
+
+    def query_errors(self, stream=None) -> int:
+        c = C.c_uint64(0)
+        _check(load().pll_query_errors(self._h, _stream_handle(stream), C.byref(c)), "pll_query_errors")
+        return int(c.value)
+
+    # ------------------------------------------------------------ exports
+    def label_entries(self) -> int:
+        c = C.c_uint64(0)
+        _check(load().pll_label_entries(self._h, C.byref(c)), "pll_label_entries")
+        return int(c.value)
+
+    def labels(self) -> Labels:
+        tot = self.label_entries()
+        off = np.empty(self.n + 1, dtype=np.uint64)
+        hubs = np.empty(max(tot, 1), dtype=np.uint32)
+        dists = np.empty(max(tot, 1), dtype=np.uint8)
+        _check(load().pll_export_labels(self._h, off.ctypes.data, hubs.ctypes.data, dists.ctypes.data),
+               "pll_export_labels")
+        return Labels(off, hubs[:tot], dists[:tot])
+
+    def bp(self):
+        nt = max(self.n * self.t, 1)
+        d = np.empty(nt, dtype=np.uint8)
+        m1 = np.empty(nt, dtype=np.uint64)
+        m0 = np.empty(nt, dtype=np.uint64)
+        _check(load().pll_export_bp(self._h, d.ctypes.data, m1.ctypes.data, m0.ctypes.data), "pll_export_bp")
+        k, shp = self.n * self.t, (self.n, self.t)
+        return d[:k].reshape(shp), m1[:k].reshape(shp), m0[:k].reshape(shp)
+
+    def bp_roots(self):
+        t = max(self.t, 1)
+        roots = np.empty(t, dtype=np.uint32)
+        cnt = np.empty(t, dtype=np.uint32)
+        S = np.empty(t * 64, dtype=np.uint32)
+        _check(load().pll_export_bp_roots(self._h, roots.ctypes.data, cnt.ctypes.data, S.ctypes.data),
+               "pll_export_bp_roots")
+        return roots[: self.t], cnt[: self.t], S[: self.t * 64].reshape(self.t, 64)
+
+    def order(self) -> np.ndarray:
+        out = np.empty(max(self.n, 1), dtype=np.uint32)
+        _check(load().pll_export_order(self._h, out.ctypes.data), "pll_export_order")
+        return out[: self.n]
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().pll_get_stats(self._h, C.byref(s)), "pll_get_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
