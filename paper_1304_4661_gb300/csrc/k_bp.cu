@@ -21,7 +21,8 @@
 //   next-level pass (E1 of level L): every u still at distance 255 for root i
 //     with some neighbour at level L joins level L+1 with the OR of those
 //     neighbours' S^{-1} and S^0.
-// The host loops until a next-level pass discovers nothing.
+// The host loops until a next-level pass discovers nothing (from level 1 on:
+// level 1 can hold only seeded members of S_r).
 #include "pll_internal.cuh"
 
 namespace pll {
@@ -163,7 +164,9 @@ int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rco
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, flag.p, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { st = cuda_status(e); break; }
-        if (*h_flag == 0) break;
+        // level 1 may consist of the seeded members of S_r alone (nothing is
+        // "discovered" from the root then), so it is always processed
+        if (*h_flag == 0 && L >= 1) break;
     }
     cudaFreeHost(h_flag);
     return st;
