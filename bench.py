@@ -36,7 +36,9 @@ WORKLOADS = {
     "rmat20": dict(kind="rmat", scale=20, ef=16, t=64, queries=10_000_000, graph_seed=1, pair_seed=3),
     # Barabasi-Albert n = 10,000, m = 4, seed 1, t = 16, 100k pairs (seed 2)
     "ba10k": dict(kind="ba", n=10_000, m=4, t=16, queries=100_000, graph_seed=1, pair_seed=2),
-    # small R-MAT for quick runs
+    # smaller R-MATs of the same family (profiling, quick runs)
+    "rmat19": dict(kind="rmat", scale=19, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
+    "rmat18": dict(kind="rmat", scale=18, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
     "rmat16": dict(kind="rmat", scale=16, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
 }
 
@@ -330,6 +332,8 @@ def run_ours(args, w, ws, rank, local):
                       "pruned": round(st["ms_pruned"], 3), "pruned_kernel": round(st["ms_pruned_kernel"], 3),
                       "finalize": round(st["ms_finalize"], 3)},
         "batches": st["batches"], "pre_cleanup": st["pre_cleanup"], "visited": st["visited"],
+        "prune_work": {"label_entries_scanned": st["pruned_scanned"], "mask_pairs": st["pruned_masks"],
+                       "arcs_expanded": st["pruned_expanded"]},
         "wall_s_timed_region": round(wall, 3),
         "clocks": clk, "e2e": e2e, "roofline": roofline,
         "gpu_launches": int(args.steps * (st["launches"] + 1)),

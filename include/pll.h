@@ -70,7 +70,7 @@ typedef struct pll_build_opts {
                             one batch; 0 = library schedule. Any value gives
                             the same labels. */
     uint32_t block;      /* threads per CTA of the pruned-BFS kernel: 128,
-                            256 or 512; 0 = library default (256). */
+                            256, 512 or 1024; 0 = library default (256). */
     uint32_t flags;      /* reserved, must be 0. */
     uint64_t reserved;   /* must be 0. */
 } pll_build_opts;

@@ -83,6 +83,7 @@ __global__ void k_append(LabelStore st, const uint64_t *__restrict__ K,
             uint32_t nc = cap * 2;
             if (nc < len + c) nc = len + c;
             if (nc < 8) nc = 8;
+            nc = (nc + 3u) & ~3u;  // every array starts on 16 bytes (vector loads)
             const unsigned long long base = atomicAdd(st.pool_top, (unsigned long long)nc);
             if (base + nc > st.pool_cap) {
                 atomicOr(err, ERR_POOL);
@@ -114,14 +115,14 @@ __global__ void k_gather_labels(uint32_t n, const uint64_t *__restrict__ soff,
 
 __global__ void k_set_u64(uint64_t *a, uint64_t idx, uint64_t val) { a[idx] = val; }
 
-__global__ void k_copy_u32(uint32_t *dst, const uint32_t *src, uint32_t n) {
+__global__ void k_widen(const uint32_t *__restrict__ in, uint64_t *out, uint32_t n, uint32_t round) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        dst[i] = src[i];
+        out[i] = (in[i] + round - 1) / round * round;
 }
 
-__global__ void k_widen(const uint32_t *__restrict__ in, uint64_t *out, uint32_t n) {
+__global__ void k_round_caps(const uint32_t *__restrict__ len, uint32_t *cap, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = in[i];
+        cap[i] = (len[i] + 3u) & ~3u;
 }
 
 inline int grid_for(uint64_t items, int block) {
@@ -164,36 +165,38 @@ int labels_append(const LabelStore &st, const uint64_t *d_kept,
     return PLL_OK;
 }
 
-// d_out[v] = sum of d_in[u] for u < v (v < n); widened in place, then scanned.
+// d_out[v] = sum of round_up(d_in[u], round) for u < v (v < n); widened in
+// place, then scanned.
 int scan_u32_to_u64(const uint32_t *d_in, uint64_t *d_out, uint32_t n, void *d_temp,
-                    size_t *temp_bytes, cudaStream_t s) {
+                    size_t *temp_bytes, cudaStream_t s, uint32_t round) {
     if (d_temp == nullptr) {
         PLL_TRY(cub::DeviceScan::ExclusiveSum(nullptr, *temp_bytes, d_out, (int64_t)n, s));
         return PLL_OK;
     }
-    k_widen<<<grid_for(n, 256), 256, 0, s>>>(d_in, d_out, n);
+    k_widen<<<grid_for(n, 256), 256, 0, s>>>(d_in, d_out, n, round);
     PLL_TRY(cudaGetLastError());
     PLL_TRY(cub::DeviceScan::ExclusiveSum(d_temp, *temp_bytes, d_out, (int64_t)n, s));
     return PLL_OK;
 }
 
-// Rewrites the pool tightly (capacity = length) into a new buffer of
-// new_cap entries. Used when the bump pointer would run past the pool.
+// Rewrites the pool (capacity = length rounded up to 4 entries, so arrays
+// stay 16-byte aligned) into a new buffer of new_cap entries. Used when the
+// bump pointer would run past the pool.
 int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s) {
     const uint32_t n = st.n;
     DevMem pool, noff, temp;
     PLL_CHECK(pool.alloc(new_cap * 4));
     PLL_CHECK(noff.alloc(((size_t)n + 1) * 8));
     size_t tb = 0;
-    PLL_CHECK(scan_u32_to_u64(st.len, noff.as<uint64_t>(), n, nullptr, &tb, s));
+    PLL_CHECK(scan_u32_to_u64(st.len, noff.as<uint64_t>(), n, nullptr, &tb, s, 4));
     PLL_CHECK(temp.alloc(tb));
-    PLL_CHECK(scan_u32_to_u64(st.len, noff.as<uint64_t>(), n, temp.p, &tb, s));
+    PLL_CHECK(scan_u32_to_u64(st.len, noff.as<uint64_t>(), n, temp.p, &tb, s, 4));
     k_gather_labels<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(n, st.off, st.len, st.pool,
                                                                     noff.as<uint64_t>(),
                                                                     pool.as<uint32_t>());
     PLL_TRY(cudaGetLastError());
     PLL_TRY(cudaMemcpyAsync(st.off, noff.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    k_copy_u32<<<grid_for(n, 256), 256, 0, s>>>(st.cap, st.len, n);
+    k_round_caps<<<grid_for(n, 256), 256, 0, s>>>(st.len, st.cap, n);
     PLL_TRY(cudaGetLastError());
     // new bump pointer = total entries = noff[n-1] + len[n-1]
     uint64_t last_off = 0;
@@ -203,7 +206,7 @@ int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s) {
         PLL_TRY(cudaMemcpyAsync(&last_len, st.len + (n - 1), 4, cudaMemcpyDeviceToHost, s));
     }
     PLL_TRY(cudaStreamSynchronize(s));
-    unsigned long long top = last_off + last_len;
+    unsigned long long top = last_off + ((last_len + 3u) & ~3u);
     PLL_TRY(cudaMemcpyAsync(st.pool_top, &top, 8, cudaMemcpyHostToDevice, s));
     PLL_TRY(cudaStreamSynchronize(s));
     cudaFree(st.pool);
@@ -220,8 +223,8 @@ int labels_finalize(const LabelStore &st, uint64_t total, uint64_t *d_off, uint3
         PLL_TRY(cudaMemsetAsync(d_off, 0, 8, s));
         return PLL_OK;
     }
-    if (d_temp == nullptr) return scan_u32_to_u64(st.len, d_off, n, nullptr, temp_bytes, s);
-    PLL_CHECK(scan_u32_to_u64(st.len, d_off, n, d_temp, temp_bytes, s));
+    if (d_temp == nullptr) return scan_u32_to_u64(st.len, d_off, n, nullptr, temp_bytes, s, 1);
+    PLL_CHECK(scan_u32_to_u64(st.len, d_off, n, d_temp, temp_bytes, s, 1));
     k_set_u64<<<1, 1, 0, s>>>(d_off, n, total);
     k_gather_labels<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(n, st.off, st.len, st.pool,
                                                                     d_off, d_lab);

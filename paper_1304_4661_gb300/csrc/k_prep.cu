@@ -18,36 +18,47 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// One warp per vertex. Checks offsets, ids, self-loops, strict ascent, and
-// that every arc (v, w) has its reverse (binary search of v in N(w)).
-__global__ void k_validate(uint32_t n, uint64_t nnz, const uint32_t *__restrict__ off,
-                           const uint32_t *__restrict__ col, uint32_t *err) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        uint32_t b = off[v], e = off[v + 1];
-        bool bad = (b > e) || (e > nnz) || (v == 0 && b != 0) || (v + 1 == n && e != nnz);
-        if (bad) {
-            if (lane == 0) atomicOr(err, ERR_CSR);
-            continue;
+// Offsets: offsets[0] = 0, non-decreasing, offsets[n] = nnz.
+__global__ void k_validate_offsets(uint32_t n, uint64_t nnz, const uint32_t *__restrict__ off,
+                                   uint32_t *err) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint32_t b = off[v], e = off[v + 1];
+        if (b > e || e > nnz || (v == 0 && b != 0) || (v + 1 == n && e != nnz)) atomicOr(err, ERR_CSR);
+    }
+}
+
+constexpr uint32_t ARCS_PER_THREAD = 8;
+
+// Arcs (valid offsets assumed): ids < n, no self-loop, strict ascent within a
+// list, and the reverse arc present (binary search of v in N(w)). Each thread
+// takes ARCS_PER_THREAD consecutive arcs, so hubs of any degree spread over
+// many threads; the source vertex is found once by binary search on offsets.
+__global__ void k_validate_arcs(uint32_t n, uint64_t nnz, const uint32_t *__restrict__ off,
+                                const uint32_t *__restrict__ col, uint32_t *err) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * ARCS_PER_THREAD;
+    for (uint64_t x0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ARCS_PER_THREAD; x0 < nnz;
+         x0 += stride) {
+        // v = last vertex with off[v] <= x0
+        uint32_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= x0) lo = mid; else hi = mid;
         }
-        for (uint32_t x = b + lane; x < e; x += 32) {
-            uint32_t w = col[x];
-            bool bd = (w >= n) || (w == v) || (x > b && col[x - 1] >= w);
-            if (!bd) {
-                uint32_t lo = off[w], hi = off[w + 1];
-                if (lo > hi || hi > nnz) {
-                    bd = true;
-                } else {
-                    while (lo < hi) {  // lower bound of v in N(w)
-                        uint32_t mid = lo + ((hi - lo) >> 1);
-                        if (col[mid] < v) lo = mid + 1; else hi = mid;
-                    }
-                    bd = !(lo < off[w + 1] && col[lo] == v);
-                }
+        uint32_t v = lo;
+        const uint64_t x1 = x0 + ARCS_PER_THREAD < nnz ? x0 + ARCS_PER_THREAD : nnz;
+        bool bad = false;
+        for (uint64_t x = x0; x < x1; ++x) {
+            while (off[v + 1] <= x) ++v;  // skip empty lists
+            const uint32_t w = col[x];
+            if (w >= n || w == v || (x > off[v] && col[x - 1] >= w)) { bad = true; break; }
+            uint32_t a = off[w], c = off[w + 1];
+            while (a < c) {  // lower bound of v in N(w)
+                const uint32_t mid = a + ((c - a) >> 1);
+                if (col[mid] < v) a = mid + 1; else c = mid;
             }
-            if (bd) atomicOr(err, ERR_CSR);
+            if (!(a < off[w + 1] && col[a] == v)) { bad = true; break; }
         }
+        if (bad) atomicOr(err, ERR_CSR);
     }
 }
 
@@ -151,7 +162,7 @@ __global__ void k_select_bp(uint32_t n, uint32_t t, const uint32_t *__restrict__
 inline int grid_for(uint64_t items, int block, int per_thread = 1) {
     uint64_t g = (items + (uint64_t)block * per_thread - 1) / ((uint64_t)block * per_thread);
     if (g < 1) g = 1;
-    if (g > 8192) g = 8192;
+    if (g > 65535) g = 65535;
     return (int)g;
 }
 
@@ -159,7 +170,13 @@ inline int grid_for(uint64_t items, int block, int per_thread = 1) {
 
 int prep_validate_csr(const Graph &g, uint32_t *d_err, cudaStream_t s) {
     if (g.n == 0) return PLL_OK;
-    k_validate<<<grid_for((uint64_t)g.n * 32, 256), 256, 0, s>>>(g.n, g.nnz, g.off, g.col, d_err);
+    k_validate_offsets<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.nnz, g.off, d_err);
+    PLL_TRY(cudaGetLastError());
+    uint32_t h = 0;
+    PLL_TRY(cudaMemcpyAsync(&h, d_err, 4, cudaMemcpyDeviceToHost, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    if (h || g.nnz == 0) return PLL_OK;  // arcs are read only behind valid offsets
+    k_validate_arcs<<<grid_for(g.nnz, 256, ARCS_PER_THREAD), 256, 0, s>>>(g.n, g.nnz, g.off, g.col, d_err);
     PLL_TRY(cudaGetLastError());
     return PLL_OK;
 }

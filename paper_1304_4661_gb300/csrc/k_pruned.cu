@@ -1,4 +1,4 @@
-// k_pruned.cu -- pruned BFSs (Alg. 1) for a batch of roots [k0, k1).
+// k_pruned.cu -- pruned BFSs (Alg. 1) for a batch of roots [k0, k0 + B).
 //
 // Alg. 2 runs Alg. 1 for k = 1..n one after another: the BFS from v_k is
 // pruned at u when Query(v_k, u, L'_{k-1}) <= P[u]. Here a whole batch of
@@ -10,97 +10,272 @@
 // L(v_k) and (h, .) in L(u) were emitted by this batch). The result is the
 // label set of the sequential algorithm for any batch size.
 //
-// One CTA ("team") runs one root at a time and pulls the next root from an
-// atomic counter. Per root:
-//   * the root's label L(v_k) (hubs < k0) goes into a shared-memory hash
-//     table: the root array T of Sec. 4.5.1 ("Querying"), so a prune test
-//     costs O(|L(u)|) shared-memory probes instead of a merge;
-//   * the root's bit-parallel row (t distances + t mask pairs) is staged in
-//     shared memory;
-//   * the BFS is level-synchronous over a per-team queue in global memory
-//     (each vertex enters at most once, so capacity n suffices); one warp
-//     tests and expands one frontier vertex: the prune test reads u's t
-//     bit-parallel distances in one coalesced load and fetches a mask pair
-//     only for roots whose distance sum could reach the bound (d~ <= d + 2,
-//     Sec. 5.3), then scans L(u) 32 entries per step; expansion reads u's
-//     neighbours 32 per step and claims unvisited ones with an atomicOr on a
-//     vertex-major bitmap [n][W] that holds one bit per root of the batch.
-//   * Visited bits live per batch root, so the bitmap is cleared once per
-//     batch instead of the per-root lazy reset of Sec. 4.5.1.
+// The BFSs of all roots of the batch advance level by level together, as
+// bulk-synchronous sweeps over one flat frontier of (root slot, vertex)
+// pairs, so the work of a level is spread over the whole GPU whatever the
+// mix of large and small BFSs:
+//
+//   init    per root: the level-0 entry (v_k, k, 0) (the root is never
+//           pruned: Query(v_k, v_k) >= 2 for v_k outside X), its visited bit,
+//           a hash table of its label L(v_k) -- the root array T of Sec.
+//           4.5.1 ("Querying"), so a prune test costs O(|L(u)|) probes -- and
+//           two 64-bit feasibility masks over the bit-parallel roots.
+//   expand  one warp per entry (u, k, d) of the level: read u's neighbours 32
+//           per step and claim the unvisited ones with an atomicOr on a
+//           vertex-major bitmap [n][W] holding one bit per root of the batch.
+//           Each lane then runs the cheap part of the prune test on its
+//           claimed neighbour w at once (it decides ~70% of candidates on
+//           power-law graphs): bit-parallel distances only -- with
+//           d~_i = d(v_k,r_i) + d(r_i,w), some d~_i <= d + 1 prunes (Sec. 5.3:
+//           the distance through {r_i} U S_{r_i} is at most d~_i). Rows of t
+//           bytes (padded to 16) arrive in 16-byte loads, four roots per
+//           instruction (saturating byte add, byte compare). The lane also
+//           records which roots could still reach the bound with their masks:
+//           d~_i = d + 2 needs a reduction of 1 (possible only if S^{-1}(v_k)
+//           or S^0(v_k) is non-empty), d~_i = d + 3 needs the S^{-1}
+//           intersection (S^{-1}(v_k) non-empty). Unpruned (slot, w) pairs
+//           and those two root masks are the next level's candidates.
+//   test    the rest of the test, one WARP per candidate so that lanes work
+//           in parallel instead of a few lanes looping alone: each lane first
+//           loads its own candidate's label offsets (32 candidates' loads in
+//           flight at once), then for each candidate in turn the lanes take
+//           the feasible bit-parallel roots (two each) and compare mask pairs;
+//           if none prunes, they take L(w)'s entries 32 at a time and probe
+//           the root's hash table. Survivors are appended as (w, k, d + 1).
+// The bitmap is cleared once per batch, instead of the per-root lazy reset of
+// Sec. 4.5.1.
+//
+// Level boundaries live in a device descriptor advanced by a one-thread
+// kernel, so the host enqueues several levels ahead and reads back only to
+// learn that the frontier is empty; sweeps over an empty range return at once.
 #include "pll_internal.cuh"
 
 namespace pll {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int HT_LOG = 12;
-constexpr uint32_t HT = 1u << HT_LOG;   // hash slots (16 KiB)
 constexpr uint32_t HT_EMPTY = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t ht_slot(uint32_t h) { return (h * 0x9E3779B1u) >> (32 - HT_LOG); }
-
-struct TeamSmem {
-    uint32_t ht[HT];
-    uint64_t bpm[2 * PLL_MAX_T];
-    uint8_t bpd[PLL_MAX_T];
-    uint32_t k;
-    uint32_t tail;
-};
-
-// Root-array lookup: distance from v_k to hub h via L(v_k), or 255.
-__device__ __forceinline__ uint32_t root_lookup(const TeamSmem &sm, bool use_ht,
-                                                const uint32_t *__restrict__ rlab, uint32_t rlen,
-                                                uint32_t h) {
-    if (use_ht) {
-        uint32_t s = ht_slot(h);
-        for (;;) {
-            uint32_t x = sm.ht[s];
-            if (x == HT_EMPTY) return INF8;
-            if (entry_hub(x) == h) return entry_dist(x);
-            s = (s + 1) & (HT - 1);
-        }
-    }
-    // long root label: binary search the sorted label in global memory
-    uint32_t lo = 0, hi = rlen;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
-    }
-    return (lo < rlen && entry_hub(rlab[lo]) == h) ? entry_dist(rlab[lo]) : INF8;
+__device__ __forceinline__ uint32_t ht_slot(uint32_t h) {
+    return (h * 0x9E3779B1u) >> (32 - BATCH_HT_LOG);
 }
 
-// Query(v_k, u) <= level ?  (bit-parallel part first, then the normal label)
-__device__ __forceinline__ bool prune_test(const PrunedBatch &b, const TeamSmem &sm, bool use_ht,
-                                           const uint32_t *__restrict__ rlab, uint32_t rlen,
-                                           uint32_t u, uint32_t level, int lane,
-                                           uint32_t &n_scan, uint32_t &n_mask) {
-    if (b.t) {
+// bytes 0x00/0xff -> 4 bits
+__device__ __forceinline__ uint32_t byte_bits(uint32_t x) {
+    const uint32_t m = x & 0x80808080u;
+    return ((m >> 7) | (m >> 14) | (m >> 21) | (m >> 28)) & 0xfu;
+}
+
+// warp-aggregated append: returns this lane's slot (valid where want is true)
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long *counter, bool want,
+                                                          int lane) {
+    const unsigned m = __ballot_sync(FULL, want);
+    unsigned long long base = 0;
+    const int leader = m ? __ffs(m) - 1 : 0;
+    if (m && lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+__global__ void k_batch_init(BatchArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < a.B; slot += warps) {
+        const uint32_t k = a.k0 + slot;
+        if (a.inX[k]) continue;  // bit-parallel vertices get no pruned BFS
+        if (lane == 0) {
+            const unsigned long long pos = atomicAdd(&a.ctr->out_n, 1ull);
+            if (pos < a.out_cap) a.out[pos] = pack_tuple(k, k, 0);
+            else atomicOr(&a.ctr->err, ERR_BUF);
+            atomicOr(&a.visited[(size_t)k * a.W + (slot >> 5)], 1u << (slot & 31));
+        }
+        // feasibility masks over the bit-parallel roots
+        uint64_t h1 = 0, h01 = 0;
+        for (uint32_t i0 = 0; i0 < a.t; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint64_t k1 = 0, kz = 0;
+            if (i < a.t) {
+                const ulonglong2 m = reinterpret_cast<const ulonglong2 *>(a.bp_m)[(size_t)k * a.t + i];
+                k1 = m.x;
+                kz = m.y;
+            }
+            h1 |= (uint64_t)__ballot_sync(FULL, k1 != 0) << i0;
+            h01 |= (uint64_t)__ballot_sync(FULL, (k1 | kz) != 0) << i0;
+        }
+        if (lane == 0) {
+            a.rootbits[2 * slot] = h1;
+            a.rootbits[2 * slot + 1] = h01;
+        }
+        // root array T as a hash table (labels longer than half the table are
+        // binary-searched instead)
+        uint32_t *ht = a.ht + (size_t)slot * BATCH_HT;
+        const uint32_t len = a.lab_len[k];
+        if (len <= BATCH_HT / 2) {
+            for (uint32_t s = lane; s < BATCH_HT; s += 32) ht[s] = HT_EMPTY;
+            __syncwarp();
+            const uint32_t *lab = a.pool + a.lab_off[k];
+            for (uint32_t j = lane; j < len; j += 32) {
+                const uint32_t e = lab[j];
+                uint32_t s = ht_slot(entry_hub(e));
+                while (atomicCAS(&ht[s], HT_EMPTY, e) != HT_EMPTY) s = (s + 1) & (BATCH_HT - 1);
+            }
+        }
+    }
+}
+
+// Cheap part of the prune test, one thread: bit-parallel distances only.
+// Returns true if some d~_i <= level; else fills c1 / c2 with the roots whose
+// masks could still bring d~_i - reduction down to level.
+__device__ __forceinline__ bool bp_distance_test(const BatchArgs &a, const uint4 (&kr)[PLL_MAX_T / 16],
+                                                 uint32_t k, uint32_t slot, uint32_t w,
+                                                 uint32_t level, uint64_t &c1, uint64_t &c2) {
+    c1 = c2 = 0;
+    if (a.t == 0) return false;
+    const uint8_t *dw = a.bp_d + (size_t)w * a.tp;
+    if (level + 2 < INF8) {
+        const uint32_t lv = level * 0x01010101u;
+        const uint32_t l1 = (level + 1) * 0x01010101u, l2 = (level + 2) * 0x01010101u;
+#pragma unroll
+        for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
+            if (c < (a.tp >> 4)) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(dw) + c);
+                const uint4 r = kr[c];
+                const uint32_t wu[4] = {q.x, q.y, q.z, q.w}, wr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t s = __vaddus4(wu[j], wr[j]);  // 255 saturates
+                    if (__vcmpleu4(s, lv)) return true;
+                    const int sh = 16 * c + 4 * j;
+                    c1 |= (uint64_t)byte_bits(__vcmpeq4(s, l1)) << sh;
+                    c2 |= (uint64_t)byte_bits(__vcmpeq4(s, l2)) << sh;
+                }
+            }
+        }
+    } else {  // depths near 255: plain loop (sums may exceed a byte)
+        const uint8_t *dk = a.bp_d + (size_t)k * a.tp;
+        for (uint32_t i = 0; i < a.t; ++i) {
+            const uint32_t x = dw[i], y = dk[i];
+            if (x == INF8 || y == INF8) continue;
+            const uint32_t td = x + y;
+            if (td <= level) return true;
+            if (td == level + 1) c1 |= 1ull << i;
+            if (td == level + 2) c2 |= 1ull << i;
+        }
+    }
+    c1 &= a.rootbits[2 * slot + 1];
+    c2 &= a.rootbits[2 * slot];
+    return false;
+}
+
+// entries [lvl_b, lvl_e) of the current level -> candidates of the next
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_batch_expand(BatchArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
+    const uint32_t level = a.desc->level;
+    uint32_t nexp = 0, nclaim = 0;
+    for (unsigned long long j = b + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < e; j += warps) {
+        const uint64_t key = a.out[j];
+        const uint32_t u = (uint32_t)(key >> 32);
+        const uint32_t k = entry_hub((uint32_t)key);
+        const uint32_t slot = k - a.k0;
+        const uint32_t sw = slot >> 5, sbit = 1u << (slot & 31);
+        // the root's distance row, kept in registers for every lane
+        uint4 kr[PLL_MAX_T / 16];
+#pragma unroll
+        for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
+            kr[c] = (c < (a.tp >> 4)) ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp) + c)
+                                      : make_uint4(~0u, ~0u, ~0u, ~0u);
+        const uint32_t eb = a.roff[u], ee = a.roff[u + 1];
+        nexp += ee - eb;
+        for (uint32_t x = eb; x < ee; x += 32) {
+            bool keep = false;
+            uint32_t w = 0;
+            uint64_t c1 = 0, c2 = 0;
+            if (x + lane < ee) {
+                w = a.rcol[x + lane];
+                uint32_t *word = &a.visited[(size_t)w * a.W + sw];
+                bool fresh = false;
+                if (!(*(volatile uint32_t *)word & sbit)) fresh = !(atomicOr(word, sbit) & sbit);
+                if (fresh) {
+                    ++nclaim;
+                    if (level + 1 >= INF8) atomicOr(&a.ctr->err, ERR_DEPTH);
+                    else keep = !bp_distance_test(a, kr, k, slot, w, level + 1, c1, c2);
+                }
+            }
+            if (__any_sync(FULL, keep)) {
+                const unsigned long long pos = warp_append(&a.ctr->cand_n, keep, lane);
+                if (keep) {
+                    if (pos < a.cand_cap) {
+                        a.cand[pos] = ((uint64_t)slot << 32) | w;
+                        reinterpret_cast<ulonglong2 *>(a.candc)[pos] = make_ulonglong2(c1, c2);
+                    } else {
+                        atomicOr(&a.ctr->err, ERR_BUF);
+                    }
+                }
+            }
+        }
+    }
+    if (lane == 0 && nexp) atomicAdd(&a.ctr->work[2], (unsigned long long)nexp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nclaim += __shfl_xor_sync(FULL, nclaim, o);
+    if (lane == 0 && nclaim) atomicAdd(&a.ctr->work[3], (unsigned long long)nclaim);
+}
+
+// One warp finishes the prune test of one candidate: lanes take the
+// feasible bit-parallel roots (two each) and compare mask pairs in one round;
+// if none prunes, lanes take L(w)'s entries 32 at a time and probe the root's
+// hash table.
+__device__ __forceinline__ bool prune_warp(const BatchArgs &a, uint32_t slot, uint32_t k, uint32_t w,
+                                           uint32_t level, uint64_t c1, uint64_t c2, uint32_t len,
+                                           uint64_t lab_off, uint32_t rlen, uint64_t rlab_off,
+                                           int lane, uint32_t &n_scan, uint32_t &n_mask) {
+    if (c1 | c2) {
+        const ulonglong2 *wm = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)w * a.t;
+        const ulonglong2 *km = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)k * a.t;
         bool p = false;
-        const size_t row = (size_t)u * b.t;
-        for (uint32_t i = lane; i < b.t; i += 32) {
-            uint32_t du = b.bp_d[row + i], dk = sm.bpd[i];
-            if (du == INF8 || dk == INF8) continue;
-            uint32_t td = du + dk;
-            if (td <= level) { p = true; continue; }
-            if (td > level + 2) continue;
-            ++n_mask;
-            ulonglong2 m = *reinterpret_cast<const ulonglong2 *>(b.bp_m + 2 * (row + i));
-            uint64_t k1 = sm.bpm[2 * i], k0 = sm.bpm[2 * i + 1];
-            uint32_t red = (k1 & m.x) ? 2u : (((k0 & m.x) | (k1 & m.y)) ? 1u : 0u);
-            if (td - red <= level) p = true;
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t i = lane + 32 * h;
+            const bool b1 = (c1 >> i) & 1, b2 = (c2 >> i) & 1;
+            if (b1 | b2) {
+                ++n_mask;
+                const ulonglong2 m = wm[i], r = km[i];
+                if (b1 && (((r.x | r.y) & m.x) | (r.x & m.y))) p = true;  // reduction >= 1
+                if (b2 && (r.x & m.x)) p = true;                          // reduction 2
+            }
         }
         if (__any_sync(FULL, p)) return true;
     }
-    const uint32_t len = b.lab_len[u];
     if (len == 0) return false;
-    const uint32_t *__restrict__ lab = b.pool + b.lab_off[u];
+    const bool use_ht = rlen <= BATCH_HT / 2;
+    const uint32_t *ht = a.ht + (size_t)slot * BATCH_HT;
+    const uint32_t *rlab = a.pool + rlab_off;
+    const uint32_t *lab = a.pool + lab_off;
     for (uint32_t j = 0; j < len; j += 32) {
         bool p = false;
         if (j + lane < len) {
             ++n_scan;
-            uint32_t e = lab[j + lane];
-            uint32_t tk = root_lookup(sm, use_ht, rlab, rlen, entry_hub(e));
-            p = (tk != INF8) && (tk + entry_dist(e) <= level);
+            const uint32_t e = lab[j + lane], h = entry_hub(e);
+            uint32_t tk = INF8;
+            if (use_ht) {
+                uint32_t s = ht_slot(h);
+                for (;;) {
+                    const uint32_t y = ht[s];
+                    if (y == HT_EMPTY) break;
+                    if (entry_hub(y) == h) { tk = entry_dist(y); break; }
+                    s = (s + 1) & (BATCH_HT - 1);
+                }
+            } else {
+                uint32_t lo = 0, hi = rlen;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
+                }
+                if (lo < rlen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
+            }
+            p = tk != INF8 && tk + entry_dist(e) <= level;
         }
         if (__any_sync(FULL, p)) return true;
     }
@@ -108,132 +283,130 @@ __device__ __forceinline__ bool prune_test(const PrunedBatch &b, const TeamSmem 
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_pruned_batch(PrunedBatch b) {
-    __shared__ TeamSmem sm;
-    constexpr int NW = BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *__restrict__ Q = b.queues + (size_t)blockIdx.x * b.n;
-
-    for (;;) {
-        if (threadIdx.x == 0) sm.k = atomicAdd(b.next_root, 1u);
-        __syncthreads();
-        const uint32_t k = sm.k;
-        if (k >= b.k1) break;
-        if (b.inX[k]) {  // bit-parallel vertices get no pruned BFS
-            __syncthreads();
-            continue;
+__global__ void __launch_bounds__(BLOCK) k_batch_test(BatchArgs a) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long b = a.desc->cand_b, e = a.desc->cand_e;
+    const uint32_t level = a.desc->level + 1;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    uint32_t n_scan = 0, n_mask = 0;
+    // warp-uniform trip count: each warp takes 32 consecutive candidates
+    const unsigned long long span = ((e - b + 31) / 32) * 32;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         i0 < span; i0 += stride) {
+        const uint32_t cnt = (uint32_t)((e - b - i0) < 32 ? (e - b - i0) : 32);
+        uint64_t mine = 0;
+        ulonglong2 mc = make_ulonglong2(0, 0);
+        uint32_t wlen = 0, klen = 0;
+        uint64_t woff = 0, koff = 0;
+        if ((uint32_t)lane < cnt) {  // per-candidate metadata, loaded in parallel
+            mine = a.cand[b + i0 + lane];
+            mc = reinterpret_cast<const ulonglong2 *>(a.candc)[b + i0 + lane];
+            const uint32_t w = (uint32_t)mine, k = a.k0 + (uint32_t)(mine >> 32);
+            wlen = a.lab_len[w];
+            woff = a.lab_off[w];
+            klen = a.lab_len[k];
+            koff = a.lab_off[k];
         }
-        const uint32_t slot = k - b.k0;
-        const uint32_t sw = slot >> 5, sbit = 1u << (slot & 31);
-
-        // stage the root: bit-parallel row and the root array T
-        for (uint32_t i = threadIdx.x; i < b.t; i += BLOCK) {
-            const size_t ri = (size_t)k * b.t + i;
-            sm.bpd[i] = b.bp_d[ri];
-            sm.bpm[2 * i] = b.bp_m[2 * ri];
-            sm.bpm[2 * i + 1] = b.bp_m[2 * ri + 1];
+        bool keep = false;
+        for (uint32_t j = 0; j < cnt; ++j) {
+            const uint64_t c = __shfl_sync(FULL, mine, j);
+            const uint32_t slot = (uint32_t)(c >> 32), w = (uint32_t)c;
+            const bool pruned = prune_warp(a, slot, a.k0 + slot, w, level, __shfl_sync(FULL, mc.x, j),
+                                           __shfl_sync(FULL, mc.y, j), __shfl_sync(FULL, wlen, j),
+                                           __shfl_sync(FULL, woff, j), __shfl_sync(FULL, klen, j),
+                                           __shfl_sync(FULL, koff, j), lane, n_scan, n_mask);
+            if (lane == (int)j) keep = !pruned;
         }
-        const uint32_t rlen = b.lab_len[k];
-        const uint32_t *__restrict__ rlab = b.pool + b.lab_off[k];
-        const bool use_ht = rlen <= HT / 2;
-        if (use_ht) {
-            for (uint32_t s = threadIdx.x; s < HT; s += BLOCK) sm.ht[s] = HT_EMPTY;
-            __syncthreads();
-            for (uint32_t j = threadIdx.x; j < rlen; j += BLOCK) {
-                uint32_t e = rlab[j];
-                uint32_t s = ht_slot(entry_hub(e));
-                while (atomicCAS(&sm.ht[s], HT_EMPTY, e) != HT_EMPTY) s = (s + 1) & (HT - 1);
+        if (__any_sync(FULL, keep)) {
+            const unsigned long long pos = warp_append(&a.ctr->out_n, keep, lane);
+            if (keep) {
+                const uint32_t slot = (uint32_t)(mine >> 32);
+                if (pos < a.out_cap) a.out[pos] = pack_tuple((uint32_t)mine, a.k0 + slot, level);
+                else atomicOr(&a.ctr->err, ERR_BUF);
             }
         }
-        if (threadIdx.x == 0) {
-            Q[0] = k;
-            atomicOr(&b.visited[(size_t)k * b.W + sw], sbit);
-            sm.tail = 1;
-        }
-        __syncthreads();
-
-        uint32_t head = 0, level = 0;
-        uint32_t n_scan = 0, n_mask = 0, n_exp = 0;  // per-thread work counters
-        for (;;) {
-            const uint32_t lvl_end = sm.tail;
-            __syncthreads();  // everyone has read tail before it grows
-            if (head >= lvl_end) break;
-            if (threadIdx.x == 0) atomicAdd(b.visit_cnt, (unsigned long long)(lvl_end - head));
-            for (uint32_t idx = head + warp; idx < lvl_end; idx += NW) {
-                const uint32_t u = Q[idx];
-                // the root is never pruned: Query(v_k, v_k) >= 2 for v_k outside X
-                if (level > 0 && prune_test(b, sm, use_ht, rlab, rlen, u, level, lane, n_scan, n_mask))
-                    continue;
-                if (lane == 0) {
-                    unsigned long long pos = atomicAdd(b.out_cnt, 1ull);
-                    if (pos < b.out_cap) b.out[pos] = pack_tuple(u, k, level);
-                    else atomicOr(b.err, ERR_BUF);
-                }
-                const uint32_t eb = b.roff[u], ee = b.roff[u + 1];
-                if (lane == 0) n_exp += ee - eb;
-                for (uint32_t x = eb; x < ee; x += 32) {
-                    bool fresh = false;
-                    uint32_t w = 0;
-                    if (x + lane < ee) {
-                        w = b.rcol[x + lane];
-                        uint32_t *word = &b.visited[(size_t)w * b.W + sw];
-                        if (!(*(volatile uint32_t *)word & sbit)) fresh = !(atomicOr(word, sbit) & sbit);
-                    }
-                    if (fresh && level + 1 >= INF8) {
-                        atomicOr(b.err, ERR_DEPTH);
-                        fresh = false;
-                    }
-                    const unsigned m = __ballot_sync(FULL, fresh);
-                    if (m) {
-                        uint32_t base = 0;
-                        if (lane == 0) base = atomicAdd(&sm.tail, (uint32_t)__popc(m));
-                        base = __shfl_sync(FULL, base, 0);
-                        if (fresh) Q[base + __popc(m & ((1u << lane) - 1u))] = w;
-                    }
-                }
-            }
-            __syncthreads();
-            head = lvl_end;
-            ++level;
-        }
-        // fold the work counters (warp sums, one atomic per warp and root)
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            n_scan += __shfl_xor_sync(FULL, n_scan, o);
-            n_mask += __shfl_xor_sync(FULL, n_mask, o);
-        }
-        if (lane == 0 && (n_scan | n_mask | n_exp)) {
-            atomicAdd(&b.work[0], (unsigned long long)n_scan);
-            atomicAdd(&b.work[1], (unsigned long long)n_mask);
-            atomicAdd(&b.work[2], (unsigned long long)n_exp);
-        }
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        n_scan += __shfl_xor_sync(FULL, n_scan, o);
+        n_mask += __shfl_xor_sync(FULL, n_mask, o);
+    }
+    if (lane == 0 && (n_scan | n_mask)) {
+        atomicAdd(&a.ctr->work[0], (unsigned long long)n_scan);
+        atomicAdd(&a.ctr->work[1], (unsigned long long)n_mask);
+    }
+}
+
+// descriptor steps between sweeps (one thread)
+__global__ void k_batch_advance(BatchArgs a, int phase) {
+    LevelDesc *d = a.desc;
+    const unsigned long long cn = a.ctr->cand_n, on = a.ctr->out_n;
+    if (phase == 0) {          // after init: level 0 = the roots
+        d->lvl_b = 0;
+        d->lvl_e = on < a.out_cap ? on : a.out_cap;
+        d->roots_n = d->lvl_e;
+        d->level = 0;
+        d->cand_b = 0;
+        d->cand_e = 0;
+    } else if (phase == 1) {   // after expand: candidates of level + 1
+        d->cand_b = d->cand_e;
+        d->cand_e = cn < a.cand_cap ? cn : a.cand_cap;
+    } else {                   // after test: survivors become the level
+        d->lvl_b = d->lvl_e;
+        d->lvl_e = on < a.out_cap ? on : a.out_cap;
+        d->level += 1;
     }
 }
 
 }  // namespace
 
-int pruned_max_grid(uint32_t block, int *grid) {
-    int dev = 0, sms = 0, per = 0;
+template <int BLOCK>
+static cudaError_t occupancy(int *pe, int *pt) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(pe, k_batch_expand<BLOCK>, BLOCK, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(pt, k_batch_test<BLOCK>, BLOCK, 0);
+    return e;
+}
+
+// grid[0]: expand sweep, grid[1]: test sweep (resident CTAs of each)
+int batch_grid(uint32_t block, int *grid) {
+    int dev = 0, sms = 0, pe = 0, pt = 0;
     PLL_TRY(cudaGetDevice(&dev));
     PLL_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaError_t e;
     switch (block) {
-        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pruned_batch<128>, 128, 0); break;
-        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pruned_batch<512>, 512, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pruned_batch<256>, 256, 0); break;
+        case 128: e = occupancy<128>(&pe, &pt); break;
+        case 512: e = occupancy<512>(&pe, &pt); break;
+        case 1024: e = occupancy<1024>(&pe, &pt); break;
+        default: e = occupancy<256>(&pe, &pt); break;
     }
     PLL_TRY(e);
-    if (per < 1) per = 1;
-    *grid = sms * per;
+    grid[0] = sms * (pe > 0 ? pe : 1);
+    grid[1] = sms * (pt > 0 ? pt : 1);
     return PLL_OK;
 }
 
-int pruned_launch(const PrunedBatch &b, int grid, uint32_t block, cudaStream_t s) {
+int batch_init(const BatchArgs &a, cudaStream_t s) {
+    const int g = (int)((a.B * 32ull + 255) / 256);
+    k_batch_init<<<g > 0 ? g : 1, 256, 0, s>>>(a);
+    k_batch_advance<<<1, 1, 0, s>>>(a, 0);
+    PLL_TRY(cudaGetLastError());
+    return PLL_OK;
+}
+
+template <int BLOCK>
+static void level_sweeps(const BatchArgs &a, const int *grid, cudaStream_t s) {
+    k_batch_expand<BLOCK><<<grid[0], BLOCK, 0, s>>>(a);
+    k_batch_advance<<<1, 1, 0, s>>>(a, 1);
+    k_batch_test<BLOCK><<<grid[1], BLOCK, 0, s>>>(a);
+    k_batch_advance<<<1, 1, 0, s>>>(a, 2);
+}
+
+int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s) {
     switch (block) {
-        case 128: k_pruned_batch<128><<<grid, 128, 0, s>>>(b); break;
-        case 512: k_pruned_batch<512><<<grid, 512, 0, s>>>(b); break;
-        default: k_pruned_batch<256><<<grid, 256, 0, s>>>(b); break;
+        case 128: level_sweeps<128>(a, grid, s); break;
+        case 512: level_sweeps<512>(a, grid, s); break;
+        case 1024: level_sweeps<1024>(a, grid, s); break;
+        default: level_sweeps<256>(a, grid, s); break;
     }
     PLL_TRY(cudaGetLastError());
     return PLL_OK;

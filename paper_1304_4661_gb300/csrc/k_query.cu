@@ -21,7 +21,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t BIG = 1u << 20;
 
 struct QueryArgs {
-    uint32_t n, t;
+    uint32_t n, t, tp;
     const uint32_t *inv;
     const uint8_t *bp_d;
     const uint64_t *bp_m;
@@ -65,12 +65,13 @@ __global__ void __launch_bounds__(256) k_query(QueryArgs a) {
         // bit-parallel distances: d~ per lane root
         uint32_t td0 = BIG, td1 = BIG;
         const size_t rs = (size_t)s * a.t, rt = (size_t)t * a.t;
+        const size_t ds = (size_t)s * a.tp, dt = (size_t)t * a.tp;
         if (lane < a.t) {
-            uint32_t x = a.bp_d[rs + lane], y = a.bp_d[rt + lane];
+            uint32_t x = a.bp_d[ds + lane], y = a.bp_d[dt + lane];
             if (x != INF8 && y != INF8) td0 = x + y;
         }
         if (lane + 32 < a.t) {
-            uint32_t x = a.bp_d[rs + lane + 32], y = a.bp_d[rt + lane + 32];
+            uint32_t x = a.bp_d[ds + lane + 32], y = a.bp_d[dt + lane + 32];
             if (x != INF8 && y != INF8) td1 = x + y;
         }
         const uint32_t dstar = warp_min(min(td0, td1));
@@ -132,7 +133,7 @@ int query_launch(const pll_index *ix, const uint32_t *d_src, const uint32_t *d_d
     uint64_t want = (q * 32 + 255) / 256;
     uint64_t cap = (uint64_t)sms * per;
     int grid = (int)(want < cap ? want : cap);
-    QueryArgs a{ix->n, ix->t, ix->d_inv, ix->d_bp_d, ix->d_bp_m, ix->d_lab_off, ix->d_lab,
+    QueryArgs a{ix->n, ix->t, ix->tp, ix->d_inv, ix->d_bp_d, ix->d_bp_m, ix->d_lab_off, ix->d_lab,
                 d_src, d_dst, q, d_out, ix->d_qerr};
     k_query<<<grid, 256, 0, s>>>(a);
     PLL_TRY(cudaGetLastError());

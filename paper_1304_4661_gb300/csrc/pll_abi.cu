@@ -5,13 +5,14 @@
 //      relabelling into rank space;
 //   2. the greedy bit-parallel root choice and t bit-parallel BFSs (Sec. 5.4,
 //      Alg. 3);
-//   3. Alg. 2 over batches of roots [k0, k1): one pruned-BFS launch for the
-//      whole batch (Alg. 1 per root, pruned with hubs < k0 and the
-//      bit-parallel labels), then sort + redundancy cleanup + append of the
-//      batch's entries; batch sizes double from 32 up to root_batch;
+//   3. Alg. 2 over batches of roots [k0, k1): the BFSs of all roots of a
+//      batch advance level by level as bulk-synchronous sweeps (Alg. 1 per
+//      root, pruned with hubs < k0 and the bit-parallel labels), then sort +
+//      redundancy cleanup + append of the batch's entries; batch sizes double
+//      from 64 up to root_batch;
 //   4. compaction of the labels into one hub-sorted CSR for queries.
-// The host reads two small counter blocks per batch (emitted-tuple count and
-// error bits; entries kept); everything else stays on the device.
+// Level boundaries stay on the device; the host reads a small counter block
+// every few levels (to see an empty frontier) and once after the append.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -28,16 +29,6 @@ int cuda_status(cudaError_t e) {
 }
 
 namespace {
-
-struct Counters {
-    unsigned long long out_cnt;
-    unsigned long long nkept;
-    unsigned long long visit_cnt;
-    unsigned long long pool_top;
-    unsigned long long work[3];  // scanned, masks, expanded (cumulative)
-    uint32_t next_root;
-    uint32_t err;
-};
 
 int err_to_status(uint32_t err) {
     if (err & ERR_CSR) return PLL_E_INVAL;
@@ -101,16 +92,19 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     const uint32_t n = ix->n;
     LabelStore st;
     st.n = n;
-    DevMem m_off, m_len, m_cap, m_pool, m_ctr;
+    DevMem m_off, m_len, m_cap, m_pool, m_ctr, m_desc;
     PLL_CHECK(m_off.alloc((size_t)n * 8));
     PLL_CHECK(m_len.alloc((size_t)n * 4));
     PLL_CHECK(m_cap.alloc((size_t)n * 4));
-    PLL_CHECK(m_ctr.alloc(sizeof(Counters)));
+    PLL_CHECK(m_ctr.alloc(sizeof(BatchCounters)));
+    PLL_CHECK(m_desc.alloc(sizeof(LevelDesc)));
     PLL_TRY(cudaMemsetAsync(m_off.p, 0, (size_t)n * 8, s));
     PLL_TRY(cudaMemsetAsync(m_len.p, 0, (size_t)n * 4, s));
     PLL_TRY(cudaMemsetAsync(m_cap.p, 0, (size_t)n * 4, s));
-    PLL_TRY(cudaMemsetAsync(m_ctr.p, 0, sizeof(Counters), s));
-    Counters *d_ctr = m_ctr.as<Counters>();
+    PLL_TRY(cudaMemsetAsync(m_ctr.p, 0, sizeof(BatchCounters), s));
+    PLL_TRY(cudaMemsetAsync(m_desc.p, 0, sizeof(LevelDesc), s));
+    BatchCounters *d_ctr = m_ctr.as<BatchCounters>();
+    LevelDesc *d_desc = m_desc.as<LevelDesc>();
     st.off = m_off.as<uint64_t>();
     st.len = m_len.as<uint32_t>();
     st.cap = m_cap.as<uint32_t>();
@@ -124,20 +118,19 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         ~PoolGuard() { if (st->pool) cudaFree(st->pool); }
     } pool_guard{&st};
 
-    // per-team BFS queues, visited bitmap, tuple buffers
-    int grid = 0;
-    PLL_CHECK(pruned_max_grid(block, &grid));
-    const uint64_t queue_budget = 6ull << 30;  // bytes
-    if ((uint64_t)grid * n * 4 > queue_budget) grid = (int)std::max<uint64_t>(1, queue_budget / ((uint64_t)n * 4));
-    DevMem m_q, m_vis, m_buf, m_sorted, m_keep, m_temp;
-    PLL_CHECK(m_q.alloc((size_t)grid * n * 4));
+    int grid[2] = {0, 0};
+    PLL_CHECK(batch_grid(block, grid));
     const uint32_t wmax = (bmax + 31) / 32;
+    DevMem m_vis, m_ht, m_bits, m_cand, m_candc, m_out, m_sorted, m_keep, m_temp;
     PLL_CHECK(m_vis.alloc((size_t)n * wmax * 4));
-    uint64_t out_cap = std::max<uint64_t>((uint64_t)n * 2, 1ull << 20);
+    PLL_CHECK(m_ht.alloc((size_t)bmax * BATCH_HT * 4));
+    PLL_CHECK(m_bits.alloc((size_t)bmax * 16));
+    uint64_t cand_cap = std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
+    uint64_t out_cap = std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
     size_t temp_bytes = 0;
     const int end_bit = 32 + std::max(1, bit_length(n - 1));
-    auto alloc_buffers = [&]() -> int {
-        PLL_CHECK(m_buf.alloc(out_cap * 8));
+    auto alloc_out = [&]() -> int {
+        PLL_CHECK(m_out.alloc(out_cap * 8));
         PLL_CHECK(m_sorted.alloc(out_cap * 8));
         PLL_CHECK(m_keep.alloc(out_cap));
         size_t a = 0, b = 0;
@@ -147,10 +140,27 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         PLL_CHECK(m_temp.alloc(temp_bytes));
         return PLL_OK;
     };
-    PLL_CHECK(alloc_buffers());
+    PLL_CHECK(m_cand.alloc(cand_cap * 8));
+    PLL_CHECK(m_candc.alloc(cand_cap * 16));
+    PLL_CHECK(alloc_out());
 
-    Counters h{};
-    uint64_t total = 0, pre = 0, visited = 0, batches = 0;
+    // pinned mirror of the counters and the level descriptor
+    struct Mirror {
+        BatchCounters c;
+        LevelDesc d;
+    };
+    Mirror *h = nullptr;
+    PLL_TRY(cudaMallocHost(&h, sizeof(Mirror)));
+    struct HostGuard {
+        Mirror *h;
+        ~HostGuard() { cudaFreeHost(h); }
+    } host_guard{h};
+    auto read_back = [&]() -> int {
+        PLL_TRY(cudaMemcpyAsync(&h->c, d_ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, s));
+        PLL_TRY(cudaMemcpyAsync(&h->d, d_desc, sizeof(LevelDesc), cudaMemcpyDeviceToHost, s));
+        PLL_TRY(cudaStreamSynchronize(s));
+        return PLL_OK;
+    };
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     PLL_TRY(cudaEventCreate(&ev0));
     PLL_TRY(cudaEventCreate(&ev1));
@@ -158,81 +168,114 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         cudaEvent_t a, b;
         ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } ev_guard{ev0, ev1};
-    uint32_t k0 = 0, B = std::min<uint32_t>(32, bmax);
+
+    uint64_t total = 0, pre = 0, batches = 0;
+    uint32_t k0 = 0, B = std::min<uint32_t>(64, bmax);
+    uint64_t last_cand = 0, last_out = 0, last_B = 1;
+    unsigned long long work0[4] = {0, 0, 0, 0};
     while (k0 < n) {
         const uint32_t k1 = (uint32_t)std::min<uint64_t>(n, (uint64_t)k0 + B);
-        const uint32_t W = (k1 - k0 + 31) / 32;
-        PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)n * W * 4, s));
-        PLL_TRY(cudaMemsetAsync(&d_ctr->out_cnt, 0, 24, s));  // out_cnt, nkept, visit_cnt
-        PLL_TRY(cudaMemcpyAsync(&d_ctr->next_root, &k0, 4, cudaMemcpyHostToDevice, s));
-        PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
-        PrunedBatch b{};
-        b.n = n; b.t = ix->t;
-        b.roff = roff; b.rcol = rcol;
-        b.bp_d = ix->d_bp_d; b.bp_m = ix->d_bp_m; b.inX = inX;
-        b.lab_off = st.off; b.lab_len = st.len; b.pool = st.pool;
-        b.k0 = k0; b.k1 = k1;
-        b.next_root = &d_ctr->next_root;
-        b.visited = m_vis.as<uint32_t>(); b.W = W;
-        b.queues = m_q.as<uint32_t>();
-        b.out = m_buf.as<uint64_t>(); b.out_cnt = &d_ctr->out_cnt; b.out_cap = out_cap;
-        b.visit_cnt = &d_ctr->visit_cnt;
-        b.work = d_ctr->work;
-        b.err = &d_ctr->err;
-        const int g = (int)std::min<uint64_t>(grid, k1 - k0);
+        // grow the buffers ahead of demand (the last batch scaled to this size)
+        {
+            const double f = 1.5 * (double)(k1 - k0) / (double)last_B;
+            if ((double)last_cand * f > (double)cand_cap) {
+                cand_cap = (uint64_t)((double)last_cand * f);
+                PLL_CHECK(m_cand.alloc(cand_cap * 8));
+                PLL_CHECK(m_candc.alloc(cand_cap * 16));
+            }
+            if ((double)last_out * f > (double)out_cap) {
+                out_cap = (uint64_t)((double)last_out * f);
+                PLL_CHECK(alloc_out());
+            }
+        }
+        BatchArgs a{};
+        a.n = n; a.t = ix->t; a.tp = ix->tp;
+        a.roff = roff; a.rcol = rcol;
+        a.bp_d = ix->d_bp_d; a.bp_m = ix->d_bp_m; a.inX = inX;
+        a.lab_off = st.off; a.lab_len = st.len; a.pool = st.pool;
+        a.k0 = k0; a.B = k1 - k0; a.W = (a.B + 31) / 32;
+        a.visited = m_vis.as<uint32_t>();
+        a.ht = m_ht.as<uint32_t>();
+        a.rootbits = m_bits.as<uint64_t>();
+        a.cand = m_cand.as<uint64_t>(); a.candc = m_candc.as<uint64_t>(); a.cand_cap = cand_cap;
+        a.out = m_out.as<uint64_t>(); a.out_cap = out_cap;
+        a.ctr = d_ctr; a.desc = d_desc;
         PLL_TRY(cudaEventRecord(ev0, s));
-        PLL_CHECK(pruned_launch(b, g, block, s));
+        PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)n * a.W * 4, s));
+        PLL_TRY(cudaMemsetAsync(d_ctr, 0, 16, s));  // cand_n, out_n
+        PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
+        PLL_CHECK(batch_init(a, s));
+        ix->stats.launches += 2;
+        // enqueue levels ahead; read back only to find the empty frontier
+        uint32_t ahead = 4;
+        for (;;) {
+            for (uint32_t l = 0; l < ahead; ++l) PLL_CHECK(batch_level(a, grid, block, s));
+            ix->stats.launches += 4ull * ahead;
+            PLL_CHECK(read_back());
+            if (h->c.err || h->d.lvl_b == h->d.lvl_e) break;
+            ahead = 2;
+        }
         PLL_TRY(cudaEventRecord(ev1, s));
-        PLL_TRY(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        PLL_TRY(cudaStreamSynchronize(s));
+        PLL_CHECK(read_back());
         {
             float ms = 0;
             PLL_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
             ix->stats.ms_pruned_kernel += ms;
             ix->stats.pruned_launches += 1;
-            ix->stats.launches += 1;
         }
-        if (h.err & ERR_DEPTH) return PLL_E_RANGE;
-        if (h.err & ERR_BUF) {  // more tuples than buffer: grow and redo the batch
-            out_cap = std::max<uint64_t>(out_cap * 2, h.out_cnt + h.out_cnt / 4);
-            PLL_CHECK(alloc_buffers());
+        if (h->c.err & ERR_DEPTH) return PLL_E_RANGE;
+        if (h->c.err & ERR_BUF) {  // a buffer overflowed: grow and redo the batch
+            PLL_TRY(cudaMemcpyAsync(d_ctr->work, work0, sizeof(work0), cudaMemcpyHostToDevice, s));
+            if (h->c.cand_n > cand_cap) {
+                cand_cap = std::max<uint64_t>(cand_cap * 2, h->c.cand_n + h->c.cand_n / 4);
+                PLL_CHECK(m_cand.alloc(cand_cap * 8));
+                PLL_CHECK(m_candc.alloc(cand_cap * 16));
+            }
+            if (h->c.out_n > out_cap) {
+                out_cap = std::max<uint64_t>(out_cap * 2, h->c.out_n + h->c.out_n / 4);
+                PLL_CHECK(alloc_out());
+            }
             continue;
         }
-        const uint64_t P = h.out_cnt;
-        visited += h.visit_cnt;
+        last_cand = h->c.cand_n;
+        last_out = h->c.out_n;
+        last_B = k1 - k0;
+        const uint64_t P = h->c.out_n;
         pre += P;
         if (P > 0) {
             // worst-case pool growth of one append: 2 x (entries + new) + 8 per run
-            const uint64_t need = h.pool_top + 2 * (total + P) + 8 * P;
+            const uint64_t need = h->c.pool_top + 2 * (total + P) + 12 * P;
             if (need > st.pool_cap) {
-                uint64_t nc = std::max<uint64_t>(st.pool_cap * 2, 3 * (total + P) + 8 * P);
+                uint64_t nc = std::max<uint64_t>(st.pool_cap * 2, 3 * (total + P) + 12 * P);
                 PLL_CHECK(labels_regrow(st, nc, s));
+                ix->stats.launches += 3;
+                ix->stats.cub_calls += 1;
             }
             size_t tb = temp_bytes;
-            PLL_CHECK(labels_sort_tuples(m_buf.as<uint64_t>(), m_sorted.as<uint64_t>(), P, end_bit,
+            PLL_CHECK(labels_sort_tuples(m_out.as<uint64_t>(), m_sorted.as<uint64_t>(), P, end_bit,
                                          m_temp.p, &tb, s));
             PLL_CHECK(labels_cleanup(m_sorted.as<uint64_t>(), P, m_keep.as<uint8_t>(), s));
             tb = temp_bytes;
             PLL_CHECK(labels_compact(m_sorted.as<uint64_t>(), m_keep.as<uint8_t>(), P,
-                                     m_buf.as<uint64_t>(), &d_ctr->nkept, m_temp.p, &tb, s));
-            PLL_CHECK(labels_append(st, m_buf.as<uint64_t>(), &d_ctr->nkept, P, &d_ctr->err, s));
+                                     m_out.as<uint64_t>(), &d_ctr->nkept, m_temp.p, &tb, s));
+            PLL_CHECK(labels_append(st, m_out.as<uint64_t>(), &d_ctr->nkept, P, &d_ctr->err, s));
             ix->stats.launches += 2;   // cleanup, append
             ix->stats.cub_calls += 2;  // sort, select
-            PLL_TRY(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-            PLL_TRY(cudaStreamSynchronize(s));
-            if (h.err & ERR_POOL) return PLL_E_NOMEM;
-            total += h.nkept;
+            PLL_CHECK(read_back());
+            if (h->c.err & ERR_POOL) return PLL_E_NOMEM;
+            total += h->c.nkept;
         }
+        for (int w = 0; w < 4; ++w) work0[w] = h->c.work[w];
         ++batches;
         k0 = k1;
         B = std::min<uint32_t>(B * 2, bmax);
     }
-    ix->stats.pruned_scanned = h.work[0];
-    ix->stats.pruned_masks = h.work[1];
-    ix->stats.pruned_expanded = h.work[2];
+    ix->stats.pruned_scanned = h->c.work[0];
+    ix->stats.pruned_masks = h->c.work[1];
+    ix->stats.pruned_expanded = h->c.work[2];
     ix->stats.label_entries = total;
     ix->stats.pre_cleanup = pre;
-    ix->stats.visited = visited;
+    ix->stats.visited = h->c.work[3];
     ix->stats.batches = batches;
     ix->entries = total;
 
@@ -266,8 +309,8 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (nnz > 0 && !col) return PLL_E_INVAL;
     if (n == 0 && nnz != 0) return PLL_E_INVAL;
     uint32_t block = o.block ? o.block : 256;
-    if (block != 128 && block != 256 && block != 512) return PLL_E_INVAL;
-    uint32_t bmax = o.root_batch ? o.root_batch : 1024;
+    if (block != 128 && block != 256 && block != 512 && block != 1024) return PLL_E_INVAL;
+    uint32_t bmax = o.root_batch ? o.root_batch : 4096;
     if (bmax > (1u << 16)) bmax = 1u << 16;
 
     pll_index *ix = new (std::nothrow) pll_index();
@@ -279,6 +322,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaGetDevice(&ix->device));
     ix->n = n;
     ix->t = o.t;
+    ix->tp = bp_stride(o.t);
     ix->nnz = nnz;
     ix->stats.n = n;
     ix->stats.t = o.t;
@@ -320,15 +364,24 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaMemsetAsync(ix->d_bp_S, 0xff, std::max<size_t>((size_t)t * BPW, 1) * 4, s));
     PLL_CHECK(prep_select_bp_roots(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(),
                                    m_inX.as<uint8_t>(), ix->d_bp_root, ix->d_bp_cnt, ix->d_bp_S, s));
+    if (n) {
+        ix->stats.launches += (nnz ? 2 : 1) + 2 + (nnz ? 3 : 2) + (t ? 1 : 0);
+        ix->stats.cub_calls += (order ? 0 : 1) + 1 + (nnz ? 1 : 0);
+    }
     ix->stats.ms_prep = tm.stop_ms();
 
     // ---- 2. bit-parallel labels
     tm.start();
     const size_t nt = (size_t)n * t;
-    PLL_TRY(cudaMalloc(&ix->d_bp_d, std::max<size_t>(nt, 1)));
+    PLL_TRY(cudaMalloc(&ix->d_bp_d, std::max<size_t>((size_t)n * ix->tp, 16)));
     PLL_TRY(cudaMalloc(&ix->d_bp_m, std::max<size_t>(nt, 1) * 16));
+    uint32_t bp_levels = 0;
     PLL_CHECK(bp_run(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), ix->d_bp_root,
-                     ix->d_bp_cnt, ix->d_bp_S, ix->d_bp_d, ix->d_bp_m, d_err, s));
+                     ix->d_bp_cnt, ix->d_bp_S, ix->d_bp_d, ix->d_bp_m, d_err, s, &bp_levels));
+    if (t && n) {
+        ix->stats.launches += 4 + 2ull * bp_levels;  // seed, chunk counts/fill, passes, finish
+        ix->stats.cub_calls += 1;
+    }
     PLL_CHECK(read_err(d_err, s, &h_err));
     if (h_err) return err_to_status(h_err);
     ix->stats.ms_bp = tm.stop_ms();
@@ -342,7 +395,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaMalloc(&ix->d_qerr, 16));
     PLL_TRY(cudaMemsetAsync(ix->d_qerr, 0, 16, s));
     PLL_TRY(cudaStreamSynchronize(s));
-    ix->stats.index_bytes = (uint64_t)n * 8 + nt * 17 + ((uint64_t)n + 1) * 8 + ix->entries * 4 +
+    ix->stats.index_bytes = (uint64_t)n * 8 + (uint64_t)n * ix->tp + nt * 16 + ((uint64_t)n + 1) * 8 + ix->entries * 4 +
                             (uint64_t)t * (BPW + 2) * 4;
     *out = ix;
     guard.ix = nullptr;
@@ -514,16 +567,17 @@ PLL_API int pll_export_bp(const pll_index *idx, uint8_t *d, uint64_t *m1, uint64
     if (t == 0 || n == 0) return PLL_OK;
     if (!d || !m1 || !m0) return PLL_E_INVAL;
     const size_t nt = (size_t)n * t;
-    std::vector<uint8_t> hd(nt);
+    const uint32_t tp = idx->tp;
+    std::vector<uint8_t> hd((size_t)n * tp);
     std::vector<uint64_t> hm(2 * nt);
     std::vector<uint32_t> inv(n);
-    PLL_TRY(cudaMemcpy(hd.data(), idx->d_bp_d, nt, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hd.data(), idx->d_bp_d, (size_t)n * tp, cudaMemcpyDeviceToHost));
     PLL_TRY(cudaMemcpy(hm.data(), idx->d_bp_m, nt * 16, cudaMemcpyDeviceToHost));
     PLL_TRY(cudaMemcpy(inv.data(), idx->d_inv, (size_t)n * 4, cudaMemcpyDeviceToHost));
     for (uint32_t v = 0; v < n; ++v) {
-        const size_t r = (size_t)inv[v] * t, o = (size_t)v * t;
+        const size_t r = (size_t)inv[v] * t, rd = (size_t)inv[v] * tp, o = (size_t)v * t;
         for (uint32_t i = 0; i < t; ++i) {
-            d[o + i] = hd[r + i];
+            d[o + i] = hd[rd + i];
             m1[o + i] = hm[2 * (r + i)];
             m0[o + i] = hm[2 * (r + i) + 1];
         }

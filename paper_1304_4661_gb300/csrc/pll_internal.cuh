@@ -8,10 +8,12 @@
 //
 // Device layouts (all in rank space, n vertices, t bit-parallel roots):
 //   roff[n+1], rcol[nnz]      CSR, neighbour lists ascending by rank
-//   bp_d[n*t]                 d_G(r_i, v), 255 = unreachable (Sec. 5.1)
+//   bp_d[n*tp]                d_G(r_i, v), 255 = unreachable (Sec. 5.1); rows
+//                             padded to tp = t rounded up to 16 bytes (pad 255)
 //   bp_m[2*(n*t)]             interleaved (S^{-1}, S^0) 64-bit sets per (v, i)
 //   label entry (uint32)      (hub rank << 8) | distance, hub rank < 2^24
-//   labels during the build   per-vertex growable arrays in one pool
+//   labels during the build   per-vertex growable arrays in one pool, each
+//                             starting on a 16-byte boundary
 //   labels after the build    CSR: lab_off[n+1] (uint64), lab[...] (uint32)
 #pragma once
 
@@ -53,10 +55,11 @@ __host__ __device__ inline uint64_t pack_tuple(uint32_t u, uint32_t k, uint32_t 
 struct pll_index {
     int device = 0;
     uint32_t n = 0, t = 0;
+    uint32_t tp = 0;               // bp_d row stride: t rounded up to 16
     uint64_t nnz = 0;
     uint32_t *d_order = nullptr;   // rank -> caller vertex id
     uint32_t *d_inv = nullptr;     // caller vertex id -> rank
-    uint8_t *d_bp_d = nullptr;     // [n][t]
+    uint8_t *d_bp_d = nullptr;     // [n][tp]
     uint64_t *d_bp_m = nullptr;    // [n][t][2]
     uint32_t *d_bp_root = nullptr; // [t] ranks (NONE = empty slot)
     uint32_t *d_bp_cnt = nullptr;  // [t]
@@ -129,13 +132,36 @@ int prep_select_bp_roots(uint32_t n, uint32_t t, const uint32_t *d_roff, const u
                          cudaStream_t s);
 
 // k_bp.cu
+inline uint32_t bp_stride(uint32_t t) { return (t + 15u) & ~15u; }
 int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
            const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S, uint8_t *d_bp_d,
-           uint64_t *d_bp_m, uint32_t *d_err, cudaStream_t s);
+           uint64_t *d_bp_m, uint32_t *d_err, cudaStream_t s, uint32_t *levels);
 
-// k_pruned.cu
-struct PrunedBatch {
-    uint32_t n, t;
+// k_pruned.cu -- batch-synchronous pruned BFS over roots [k0, k0 + B)
+constexpr int BATCH_HT_LOG = 9;
+constexpr uint32_t BATCH_HT = 1u << BATCH_HT_LOG;  // hash slots per root label
+
+struct BatchCounters {
+    unsigned long long cand_n;    // candidates appended (all levels of the batch)
+    unsigned long long out_n;     // entries (u, k, d) appended
+    unsigned long long work[4];   // label entries scanned, mask pairs, arcs, vertices
+                                  // claimed (cumulative)
+    unsigned long long nkept;     // entries kept by the cleanup
+    unsigned long long pool_top;  // label pool bump pointer
+    uint32_t err;
+    uint32_t pad;
+};
+
+struct LevelDesc {
+    unsigned long long lvl_b, lvl_e;    // entries of the current level
+    unsigned long long cand_b, cand_e;  // candidates of the next level
+    unsigned long long roots_n;         // level-0 entries
+    uint32_t level;
+    uint32_t pad;
+};
+
+struct BatchArgs {
+    uint32_t n, t, tp;
     const uint32_t *roff, *rcol;
     const uint8_t *bp_d;
     const uint64_t *bp_m;
@@ -143,20 +169,21 @@ struct PrunedBatch {
     const uint64_t *lab_off;   // per-vertex start in pool
     const uint32_t *lab_len;   // per-vertex length (entries with hub < k0)
     const uint32_t *pool;
-    uint32_t k0, k1;           // roots of this batch: ranks [k0, k1)
-    uint32_t *next_root;       // work counter, starts at k0
+    uint32_t k0, B, W;         // roots [k0, k0 + B), W = ceil(B / 32)
     uint32_t *visited;         // [n][W] bitmap, one bit per batch root
-    uint32_t W;
-    uint32_t *queues;          // [grid][n]
-    uint64_t *out;             // pre-cleanup tuples
-    unsigned long long *out_cnt;
-    uint64_t out_cap;
-    unsigned long long *visit_cnt;
-    unsigned long long *work;  // [0] label entries scanned, [1] mask pairs, [2] arcs expanded
-    uint32_t *err;
+    uint32_t *ht;              // [B][BATCH_HT] root label hash tables
+    uint64_t *rootbits;        // [B][2] feasibility masks
+    uint64_t *cand;            // (slot << 32 | vertex), all levels
+    uint64_t *candc;           // [cand_cap][2] roots whose masks may still prune
+    unsigned long long cand_cap;
+    uint64_t *out;             // entries (u << 32 | k << 8 | d), all levels
+    unsigned long long out_cap;
+    BatchCounters *ctr;
+    LevelDesc *desc;
 };
-int pruned_max_grid(uint32_t block, int *grid);
-int pruned_launch(const PrunedBatch &b, int grid, uint32_t block, cudaStream_t s);
+int batch_grid(uint32_t block, int *grid);  // grid[2]: expand, test
+int batch_init(const BatchArgs &a, cudaStream_t s);
+int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s);
 
 // k_labels.cu
 struct LabelStore {
@@ -180,7 +207,7 @@ int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s);
 int labels_finalize(const LabelStore &st, uint64_t total, uint64_t *d_off, uint32_t *d_lab,
                     void *d_temp, size_t *temp_bytes, cudaStream_t s);
 int scan_u32_to_u64(const uint32_t *d_in, uint64_t *d_out, uint32_t n, void *d_temp,
-                    size_t *temp_bytes, cudaStream_t s);
+                    size_t *temp_bytes, cudaStream_t s, uint32_t round);
 
 // k_query.cu
 int query_launch(const pll_index *ix, const uint32_t *d_src, const uint32_t *d_dst, uint64_t q,
