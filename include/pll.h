@@ -23,10 +23,10 @@
  *     default stream). Functions marked "synchronous" wait for that stream
  *     before they return.
  *   - Every function returns a pll_status; no C++ exception crosses the ABI.
- *     On failure no output is valid and nothing is leaked. The library holds
- *     no global mutable state between calls; an index is immutable after
- *     pll_build, so queries on one index may run concurrently on different
- *     streams.
+ *     On failure no output is valid and nothing is leaked. Apart from the
+ *     scratch array of pll_bp_labels_noalloc, the library holds no global
+ *     mutable state between calls; an index is immutable after pll_build, so
+ *     queries on one index may run concurrently on different streams.
  */
 #ifndef PLL_H
 #define PLL_H
@@ -179,6 +179,45 @@ PLL_API int pll_export_bp(const pll_index *idx, uint8_t *d, uint64_t *m1, uint64
 PLL_API int pll_export_bp_roots(const pll_index *idx, uint32_t *roots, uint32_t *cnt,
                                 uint32_t *S);
 PLL_API int pll_export_order(const pll_index *idx, uint32_t *order);
+
+/* Scratch that pll_bp_labels_noalloc keeps in device memory (64 MiB). */
+#define PLL_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * pll_bp_labels_noalloc -- the bit-parallel labels that pll_build computes
+ * (the greedy choice of roots r_i and neighbour sets S_{r_i}, then one
+ * bit-parallel BFS per root), produced without allocating anything. The
+ * paper has no counterpart: the entry point is for callers that cannot call
+ * cudaMalloc -- their device memory belongs to another allocator (a
+ * framework's caching allocator may hold nearly the whole GPU), or their
+ * process forbids allocation once it runs. It allocates no device or host
+ * memory and calls no allocating library routine.
+ *
+ *   rank_offsets, rank_cols  device; the graph with vertices relabelled so that
+ *                  vertex id == rank in the vertex order (same CSR rules as
+ *                  pll_build; it is checked, PLL_E_INVAL if malformed).
+ *   n, nnz, t      n >= 1, 1 <= t <= PLL_MAX_T.
+ *   d              device uint8[n * tp], tp = t rounded up to a multiple of 16:
+ *                  d[v * tp + i] = d_G(r_i, v), 255 if unreachable; the bytes
+ *                  t..tp-1 of each row are set to 255.
+ *   masks          device uint64[n * t * 2]: masks[2 * (v * t + i)] = S^{-1},
+ *                  masks[2 * (v * t + i) + 1] = S^0 of (r_i, v).
+ *   roots, cnt, S  device uint32[t], uint32[t], uint32[t * 64]: as
+ *                  pll_export_bp_roots, with ranks as vertex ids.
+ *
+ * The values equal those of pll_build for the same order and t. Scratch is
+ * one file-scope device array of PLL_NOALLOC_SCRATCH_BYTES, held by every GPU
+ * that loads the library until the process exits; a call needs about
+ * 13 * n + nnz / 64 bytes of it plus a few KiB, and returns PLL_E_RANGE if the
+ * graph does not fit. The first call on a device (with that device current)
+ * looks up the array's device address once; make that first call before any
+ * stream capture. All calls share the array, so calls that overlap on the GPU
+ * race. Synchronous.
+ */
+PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *rank_cols,
+                                  uint32_t n, uint64_t nnz, uint32_t t, uint8_t *d,
+                                  uint64_t *masks, uint32_t *roots, uint32_t *cnt, uint32_t *S,
+                                  void *stream);
 
 /* Build statistics (sizes, per-phase times in milliseconds). */
 PLL_API int pll_get_stats(const pll_index *idx, pll_stats *out);

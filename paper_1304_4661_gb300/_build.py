@@ -27,6 +27,7 @@ CU_SOURCES = [
     "k_pruned.cu",
     "k_labels.cu",
     "k_query.cu",
+    "pll_noalloc.cu",
 ]
 
 

@@ -271,3 +271,78 @@ int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rco
 }
 
 }  // namespace pll
+
+namespace pll {
+
+// The same bit-parallel stage as bp_run, for callers that provide all device
+// scratch: nothing is allocated (the level flag is read into a host stack
+// variable). scratch must be 256-byte aligned and at least
+// bp_scratch_bytes(n, nnz) long; S-members / roots must already be chosen.
+size_t bp_scratch_bytes(uint32_t n, uint64_t nnz, size_t *cub_bytes) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, (uint32_t *)nullptr, (uint32_t *)nullptr, (int)n + 1);
+    if (cub_bytes) *cub_bytes = tb;
+    const size_t items = (size_t)n + (nnz + CHUNK - 1) / CHUNK;
+    return up(((size_t)n + 1) * 4) * 2 + up(items * 4) + up(8) + up(tb);
+}
+
+int bp_run_in(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
+              uint64_t nnz, const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S,
+              uint8_t *d_bp_d, uint64_t *d_bp_m, uint32_t *d_err, void *scratch,
+              size_t scratch_bytes, cudaStream_t s) {
+    if (t == 0 || n == 0) return PLL_OK;
+    if (t > PLL_MAX_T) return PLL_E_RANGE;
+    size_t tb = 0;
+    if (bp_scratch_bytes(n, nnz, &tb) > scratch_bytes) return PLL_E_RANGE;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    unsigned char *p = static_cast<unsigned char *>(scratch);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(p);
+    p += up(((size_t)n + 1) * 4);
+    uint32_t *coff = reinterpret_cast<uint32_t *>(p);
+    p += up(((size_t)n + 1) * 4);
+    uint32_t *items = reinterpret_cast<uint32_t *>(p);
+    p += up(((size_t)n + (nnz + CHUNK - 1) / CHUNK) * 4);
+    uint32_t *flag = reinterpret_cast<uint32_t *>(p);
+    p += up(8);
+    void *cub_temp = p;
+
+    const size_t nt = (size_t)n * t;
+    const uint32_t tp = bp_stride(t);
+    PLL_TRY(cudaMemsetAsync(d_bp_d, 0xff, (size_t)n * tp, s));
+    PLL_TRY(cudaMemsetAsync(d_bp_m, 0, nt * 16, s));
+    k_bp_seed<<<t, BPW, 0, s>>>(t, tp, d_root, d_cnt, d_S, d_bp_d, d_bp_m);
+    PLL_TRY(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));
+    const int g1 = (int)std::min<uint64_t>((n + 255) / 256, 65535);
+    k_chunk_counts<<<g1, 256, 0, s>>>(n, d_roff, cnt);
+    PLL_TRY(cub::DeviceScan::ExclusiveSum(cub_temp, tb, cnt, coff, (int)n + 1, s));
+    uint32_t nitems = 0;
+    PLL_TRY(cudaMemcpyAsync(&nitems, coff + n, 4, cudaMemcpyDeviceToHost, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    k_chunk_fill<<<g1, 256, 0, s>>>(n, coff, items);
+    PLL_TRY(cudaGetLastError());
+    int dev = 0, sms = 148;
+    PLL_TRY(cudaGetDevice(&dev));
+    PLL_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint64_t want = ((uint64_t)nitems * 32 + 255) / 256;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 16));
+    BpArgs a{n, t, tp, 0, d_roff, d_rcol, items, coff, nitems, d_bp_d, d_bp_m, flag, d_err};
+    for (uint32_t L = 0; L < INF8; ++L) {
+        a.L = L;
+        PLL_TRY(cudaMemsetAsync(flag, 0, 4, s));
+        k_bp_same_level<<<grid, 256, 0, s>>>(a);
+        k_bp_next_level<<<grid, 256, 0, s>>>(a);
+        PLL_TRY(cudaGetLastError());
+        uint32_t h_flag = 0;
+        PLL_TRY(cudaMemcpyAsync(&h_flag, flag, 4, cudaMemcpyDeviceToHost, s));
+        PLL_TRY(cudaStreamSynchronize(s));
+        if (h_flag == 0 && L >= 1) break;
+    }
+    k_bp_finish<<<(int)std::min<size_t>((nt + 255) / 256, (size_t)sms * 32), 256, 0, s>>>(
+        nt, reinterpret_cast<ulonglong2 *>(d_bp_m));
+    PLL_TRY(cudaGetLastError());
+    PLL_TRY(cudaStreamSynchronize(s));
+    return PLL_OK;
+}
+
+}  // namespace pll

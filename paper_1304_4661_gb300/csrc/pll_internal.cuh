@@ -137,6 +137,13 @@ int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rco
            const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S, uint8_t *d_bp_d,
            uint64_t *d_bp_m, uint32_t *d_err, cudaStream_t s, uint32_t *levels);
 
+// k_bp.cu, for pll_bp_labels_noalloc: the same stage on caller scratch
+size_t bp_scratch_bytes(uint32_t n, uint64_t nnz, size_t *cub_bytes);
+int bp_run_in(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
+              uint64_t nnz, const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S,
+              uint8_t *d_bp_d, uint64_t *d_bp_m, uint32_t *d_err, void *scratch,
+              size_t scratch_bytes, cudaStream_t s);
+
 // k_pruned.cu -- batch-synchronous pruned BFS over roots [k0, k0 + B)
 constexpr int BATCH_HT_LOG = 9;
 constexpr uint32_t BATCH_HT = 1u << BATCH_HT_LOG;  // hash slots per root label

@@ -24,7 +24,9 @@ SYMBOLS = [
     "pll_build", "pll_build_host", "pll_query", "pll_query_async", "pll_query_errors",
     "pll_query_host", "pll_label_entries", "pll_export_labels", "pll_export_bp",
     "pll_export_bp_roots", "pll_export_order", "pll_get_stats", "pll_free", "pll_status_str",
+    "pll_bp_labels_noalloc",
 ]
+PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class BuildOpts(C.Structure):
@@ -95,6 +97,8 @@ def load(build_if_missing: bool = True):
     lib.pll_free.argtypes = [vp]
     lib.pll_status_str.restype = C.c_char_p
     lib.pll_status_str.argtypes = [i32]
+    lib.pll_bp_labels_noalloc.restype = i32
+    lib.pll_bp_labels_noalloc.argtypes = [vp, vp, u32, u64, u32, vp, vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -129,6 +133,17 @@ def _dptr(x):
 def _hptr(a, dtype):
     a = np.ascontiguousarray(np.asarray(a, dtype=dtype))
     return a, a.ctypes.data
+
+
+def bp_labels_noalloc(rank_offsets, rank_cols, t: int, d, masks, roots, cnt, S, stream=None):
+    """pll_bp_labels_noalloc on CUDA tensors (outputs preallocated by the caller):
+    d uint8[n * tp] (tp = t rounded up to 16), masks uint64[n * t * 2],
+    roots/cnt uint32[t], S uint32[t * 64]; ids are ranks."""
+    n = int(rank_offsets.shape[0]) - 1
+    nnz = int(rank_cols.shape[0])
+    _check(load().pll_bp_labels_noalloc(_dptr(rank_offsets), _dptr(rank_cols) if nnz else None, n,
+                                        nnz, t, _dptr(d), _dptr(masks), _dptr(roots), _dptr(cnt),
+                                        _dptr(S), _stream_handle(stream)), "pll_bp_labels_noalloc")
 
 
 @dataclass
