@@ -286,32 +286,42 @@ def run_ours(args, w, ws, rank, local):
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    launches = max(st["pruned_launches"], 1)
-    pr_bytes = (st["visited"] * (8 + 12 + t) + st["pruned_masks"] * 16 + st["pruned_scanned"] * 4
-                + st["pruned_expanded"] * 8 + st["pre_cleanup"] * 8)
-    pr_ms = st["ms_pruned_kernel"]
     q = w["queries"]
+    tp = (t + 15) // 16 * 16
+    # algorithmic bytes of each kernel over one build (per-unit figures x the
+    # units the kernels count), divided over its launches
+    exp_bytes = (st["pre_cleanup"] * (8 + 8 + tp) + st["pruned_expanded"] * (4 + 4)
+                 + st["visited"] * tp + st["candidates"] * 24)
+    test_bytes = (st["candidates"] * (24 + 24) + st["pruned_masks"] * 16
+                  + st["pruned_scanned"] * (4 + 4) + st["pre_cleanup"] * 8)
     # per pair: ids (8), ranks (8), 2 x t distance bytes, 4 label offsets (32),
     # the result byte, and both labels (4 bytes per entry; Lsz is by vertex id)
     q_bytes = q * (8 + 8 + 2 * t + 32 + 1) + 4 * int(Lsz[s].sum() + Lsz[u].sum())
     kern = {
-        "k_pruned_batch": {"ms_per_step": pr_ms, "launches": st["pruned_launches"],
-                           "bytes_per_launch": pr_bytes / launches,
-                           "ms_per_launch": pr_ms / launches},
-        "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes_per_launch": q_bytes,
-                    "ms_per_launch": qk_ms},
+        "k_batch_test": {"ms_per_step": st["ms_test"], "launches": st["test_launches"],
+                         "bytes": test_bytes},
+        "k_batch_expand": {"ms_per_step": st["ms_expand"], "launches": st["expand_launches"],
+                           "bytes": exp_bytes},
+        "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes": q_bytes},
     }
+    for v in kern.values():
+        v["launches"] = max(v["launches"], 1)
+        v["bytes_per_launch"] = v["bytes"] / v["launches"]
+        v["ms_per_launch"] = v["ms_per_step"] / v["launches"]
+        v["achieved_gbs"] = v["bytes"] / max(v["ms_per_step"], 1e-9) / 1e6
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
     kd = kern[dom]
-    achieved = kd["bytes_per_launch"] / (kd["ms_per_launch"] * 1e-3) / 1e9
+    achieved = kd["achieved_gbs"]
     src = os.path.join(ROOT, "paper_1304_4661_gb300", "csrc",
-                       "k_pruned.cu" if dom == "k_pruned_batch" else "k_query.cu")
+                       "k_query.cu" if dom == "k_query" else "k_pruned.cu")
     prof = PROFILED.get(dom)
     traffic = prof["dram_bytes_per_launch"] if prof and prof["src_sha"] == file_sha(src) else None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": traffic,
-                "others": {k: {"achieved_gbs": round(v["bytes_per_launch"] / (v["ms_per_launch"] * 1e-3) / 1e9, 1),
+                "algorithmic_bytes_per_launch": round(kd["bytes_per_launch"]),
+                "launch_ms": round(kd["ms_per_launch"], 4),
+                "others": {k: {"achieved_gbs": round(v["achieved_gbs"], 1),
                                "ms_per_step": round(v["ms_per_step"], 3), "launches": v["launches"]}
                            for k, v in kern.items()}}
 
@@ -329,11 +339,12 @@ def run_ours(args, w, ws, rank, local):
         "label_entries_per_s": round(st["label_entries"] / (build_ms * 1e-3), 1),
         "avg_label": round(st["label_entries"] / max(g.n, 1), 2),
         "phases_ms": {"prep": round(st["ms_prep"], 3), "bp": round(st["ms_bp"], 3),
-                      "pruned": round(st["ms_pruned"], 3), "pruned_kernel": round(st["ms_pruned_kernel"], 3),
+                      "pruned": round(st["ms_pruned"], 3), "pruned_bfs": round(st["ms_pruned_kernel"], 3),
+                      "expand_sweeps": round(st["ms_expand"], 3), "test_sweeps": round(st["ms_test"], 3),
                       "finalize": round(st["ms_finalize"], 3)},
         "batches": st["batches"], "pre_cleanup": st["pre_cleanup"], "visited": st["visited"],
         "prune_work": {"label_entries_scanned": st["pruned_scanned"], "mask_pairs": st["pruned_masks"],
-                       "arcs_expanded": st["pruned_expanded"]},
+                       "arcs_expanded": st["pruned_expanded"], "candidates": st["candidates"]},
         "wall_s_timed_region": round(wall, 3),
         "clocks": clk, "e2e": e2e, "roofline": roofline,
         "gpu_launches": int(args.steps * (st["launches"] + 1)),

@@ -98,6 +98,12 @@ typedef struct pll_stats {
     uint64_t launches;           /* kernels of this library launched by the build
                                     (not counting CUB's) */
     uint64_t cub_calls;          /* CUB device-wide sorts, scans, selects */
+    /* the two sweeps of the pruned stage, CUDA-event time summed over launches */
+    double ms_expand;            /* expand sweeps (claim + distance check) */
+    double ms_test;              /* test sweeps (masks + labels) */
+    uint64_t expand_launches;
+    uint64_t test_launches;
+    uint64_t candidates;         /* candidates passed from expand to test */
 } pll_stats;
 
 /*

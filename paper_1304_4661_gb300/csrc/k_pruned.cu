@@ -33,8 +33,11 @@
 //           records which roots could still reach the bound with their masks:
 //           d~_i = d + 2 needs a reduction of 1 (possible only if S^{-1}(v_k)
 //           or S^0(v_k) is non-empty), d~_i = d + 3 needs the S^{-1}
-//           intersection (S^{-1}(v_k) non-empty). Unpruned (slot, w) pairs
-//           and those two root masks are the next level's candidates.
+//           intersection (S^{-1}(v_k) non-empty). The lane then checks the
+//           masks of the first QUICK roots itself: roots come in rank order,
+//           so these are the largest hubs and they decide most mask tests.
+//           Unpruned (slot, w) pairs and the remaining feasible roots are the
+//           next level's candidates.
 //   test    the rest of the test, one WARP per candidate so that lanes work
 //           in parallel instead of a few lanes looping alone: each lane first
 //           loads its own candidate's label offsets (32 candidates' loads in
@@ -167,6 +170,32 @@ __device__ __forceinline__ bool bp_distance_test(const BatchArgs &a, const uint4
     return false;
 }
 
+// Masks of the first QUICK bit-parallel roots, one thread. The roots are
+// chosen in rank order (Sec. 5.4), so the first ones are the largest hubs and
+// settle most mask tests; checking them here keeps most candidates out of
+// the test sweep and away from the rest of their 1 KiB mask rows. Clears
+// those roots from c1 / c2.
+constexpr uint32_t QUICK = 4;
+__device__ __forceinline__ bool quick_masks(const BatchArgs &a, uint32_t k, uint32_t w, uint64_t &c1,
+                                            uint64_t &c2) {
+    const uint32_t q1 = (uint32_t)c1 & ((1u << QUICK) - 1u), q2 = (uint32_t)c2 & ((1u << QUICK) - 1u);
+    c1 &= ~(uint64_t)((1u << QUICK) - 1u);
+    c2 &= ~(uint64_t)((1u << QUICK) - 1u);
+    if (!(q1 | q2)) return false;
+    const ulonglong2 *wm = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)w * a.t;
+    const ulonglong2 *km = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)k * a.t;
+    bool p = false;
+#pragma unroll
+    for (uint32_t i = 0; i < QUICK; ++i) {
+        if (((q1 | q2) >> i) & 1u) {
+            const ulonglong2 m = wm[i], r = km[i];
+            if (((q1 >> i) & 1u) && ((((r.x | r.y) & m.x) | (r.x & m.y)) != 0)) p = true;
+            if (((q2 >> i) & 1u) && ((r.x & m.x) != 0)) p = true;
+        }
+    }
+    return p;
+}
+
 // entries [lvl_b, lvl_e) of the current level -> candidates of the next
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_batch_expand(BatchArgs a) {
@@ -201,7 +230,8 @@ __global__ void __launch_bounds__(BLOCK) k_batch_expand(BatchArgs a) {
                 if (fresh) {
                     ++nclaim;
                     if (level + 1 >= INF8) atomicOr(&a.ctr->err, ERR_DEPTH);
-                    else keep = !bp_distance_test(a, kr, k, slot, w, level + 1, c1, c2);
+                    else keep = !bp_distance_test(a, kr, k, slot, w, level + 1, c1, c2) &&
+                                !quick_masks(a, k, w, c1, c2);
                 }
             }
             if (__any_sync(FULL, keep)) {
@@ -394,19 +424,25 @@ int batch_init(const BatchArgs &a, cudaStream_t s) {
 }
 
 template <int BLOCK>
-static void level_sweeps(const BatchArgs &a, const int *grid, cudaStream_t s) {
+static void level_sweeps(const BatchArgs &a, const int *grid, cudaStream_t s, cudaEvent_t *ev) {
+    if (ev) cudaEventRecord(ev[0], s);
     k_batch_expand<BLOCK><<<grid[0], BLOCK, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[1], s);
     k_batch_advance<<<1, 1, 0, s>>>(a, 1);
+    if (ev) cudaEventRecord(ev[2], s);
     k_batch_test<BLOCK><<<grid[1], BLOCK, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[3], s);
     k_batch_advance<<<1, 1, 0, s>>>(a, 2);
 }
 
-int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s) {
+// ev: null, or four events recorded around the expand and test sweeps
+int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s,
+                cudaEvent_t *ev) {
     switch (block) {
-        case 128: level_sweeps<128>(a, grid, s); break;
-        case 512: level_sweeps<512>(a, grid, s); break;
-        case 1024: level_sweeps<1024>(a, grid, s); break;
-        default: level_sweeps<256>(a, grid, s); break;
+        case 128: level_sweeps<128>(a, grid, s, ev); break;
+        case 512: level_sweeps<512>(a, grid, s, ev); break;
+        case 1024: level_sweeps<1024>(a, grid, s, ev); break;
+        default: level_sweeps<256>(a, grid, s, ev); break;
     }
     PLL_TRY(cudaGetLastError());
     return PLL_OK;

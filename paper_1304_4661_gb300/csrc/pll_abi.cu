@@ -164,10 +164,17 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     PLL_TRY(cudaEventCreate(&ev0));
     PLL_TRY(cudaEventCreate(&ev1));
+    cudaEvent_t sweep_ev[16] = {};
+    for (auto &e : sweep_ev) PLL_TRY(cudaEventCreate(&e));
     struct EvGuard {
         cudaEvent_t a, b;
-        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
-    } ev_guard{ev0, ev1};
+        cudaEvent_t *sw;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            for (int i = 0; i < 16; ++i) if (sw[i]) cudaEventDestroy(sw[i]);
+        }
+    } ev_guard{ev0, ev1, sweep_ev};
 
     uint64_t total = 0, pre = 0, batches = 0;
     uint32_t k0 = 0, B = std::min<uint32_t>(64, bmax);
@@ -206,12 +213,23 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
         PLL_CHECK(batch_init(a, s));
         ix->stats.launches += 2;
-        // enqueue levels ahead; read back only to find the empty frontier
+        // enqueue levels ahead; read back only to find the empty frontier.
+        // Events around every expand and test sweep give their device times.
         uint32_t ahead = 4;
         for (;;) {
-            for (uint32_t l = 0; l < ahead; ++l) PLL_CHECK(batch_level(a, grid, block, s));
+            for (uint32_t l = 0; l < ahead; ++l)
+                PLL_CHECK(batch_level(a, grid, block, s, sweep_ev + 4 * l));
             ix->stats.launches += 4ull * ahead;
             PLL_CHECK(read_back());
+            for (uint32_t l = 0; l < ahead; ++l) {
+                float me = 0, mt = 0;
+                PLL_TRY(cudaEventElapsedTime(&me, sweep_ev[4 * l], sweep_ev[4 * l + 1]));
+                PLL_TRY(cudaEventElapsedTime(&mt, sweep_ev[4 * l + 2], sweep_ev[4 * l + 3]));
+                ix->stats.ms_expand += me;
+                ix->stats.ms_test += mt;
+            }
+            ix->stats.expand_launches += ahead;
+            ix->stats.test_launches += ahead;
             if (h->c.err || h->d.lvl_b == h->d.lvl_e) break;
             ahead = 2;
         }
@@ -237,6 +255,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             }
             continue;
         }
+        ix->stats.candidates += h->c.cand_n;
         last_cand = h->c.cand_n;
         last_out = h->c.out_n;
         last_B = k1 - k0;

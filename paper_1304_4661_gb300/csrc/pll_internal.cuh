@@ -190,7 +190,8 @@ struct BatchArgs {
 };
 int batch_grid(uint32_t block, int *grid);  // grid[2]: expand, test
 int batch_init(const BatchArgs &a, cudaStream_t s);
-int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s);
+int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s,
+                cudaEvent_t *ev);
 
 // k_labels.cu
 struct LabelStore {

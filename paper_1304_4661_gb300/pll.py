@@ -42,7 +42,10 @@ class Stats(C.Structure):
                 ("ms_finalize", C.c_double), ("ms_pruned_kernel", C.c_double),
                 ("pruned_launches", C.c_uint64), ("pruned_scanned", C.c_uint64),
                 ("pruned_masks", C.c_uint64), ("pruned_expanded", C.c_uint64),
-                ("launches", C.c_uint64), ("cub_calls", C.c_uint64)]
+                ("launches", C.c_uint64), ("cub_calls", C.c_uint64),
+                ("ms_expand", C.c_double), ("ms_test", C.c_double),
+                ("expand_launches", C.c_uint64), ("test_launches", C.c_uint64),
+                ("candidates", C.c_uint64)]
 
 
 class PLLError(RuntimeError):
