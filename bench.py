@@ -44,7 +44,11 @@ WORKLOADS = {
 
 # DRAM bytes per launch of the pruned-BFS kernel measured by ncu, valid only
 # for the kernel source with this hash (else traffic is reported as null).
-PROFILED = {}
+PROFILED = {
+    # ncu, all 1150 launches of one R-MAT-20 build (profiles/k_batch_sweeps_rmat20.md)
+    "k_batch_expand": {"src_sha": "a6dd14a9fcfbabc5", "dram_bytes_per_launch": 153787301},
+    "k_batch_test": {"src_sha": "a6dd14a9fcfbabc5", "dram_bytes_per_launch": 129301271},
+}
 
 
 def make_graph(w):
