@@ -360,6 +360,85 @@ def run_ours(args, w, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------- multi-graph batch
+def run_batch(args, ws, rank, local):
+    """256 uneven graphs (half Barabasi-Albert n log-uniform 1k-50k, m 2-8;
+    half Watts-Strogatz n log-uniform 1k-50k, k = 6, p = 0.1), t = 16:
+    one pll_build per graph vs one pll_build_batch over their union, with the
+    library defaults and with the autotuner's choice."""
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+    t = 16
+    specs = gg.batch_specs(256, seed=4)
+    gl = [gg.make(sp) for sp in specs]
+    off, col, start = gg.union(gl)
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    d_off, d_col = dev(off), dev(col)
+    per = [(dev(g.offsets), dev(g.cols)) for g in gl]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def sequential():
+        total = 0
+        for o, c in per:
+            ix = pll.Index.build(o, c, t=t)
+            total += ix.label_entries()
+            ix.close()
+        return total
+
+    def batched(rb=0, bl=0):
+        ix = pll.Index.build_batch(d_off, d_col, start, t=t, root_batch=rb, block=bl)
+        e = ix.label_entries()
+        ix.close()
+        return e
+
+    for _ in range(args.warmup):
+        sequential()
+        batched()
+    seq = [timed(sequential) for _ in range(args.steps)]
+    bat = [timed(batched) for _ in range(args.steps)]
+    tune_ms_wall = time.perf_counter()
+    rb, bl, tuned_trial_ms = pll.autotune(d_off, d_col, t, graph_start=start)
+    tune_ms_wall = (time.perf_counter() - tune_ms_wall) * 1e3
+    tun = [timed(lambda: batched(rb, bl)) for _ in range(args.steps)]
+    assert seq[0][1] == bat[0][1] == tun[0][1], "label counts differ between builds"
+    seq_ms = statistics.mean(x[0] for x in seq)
+    bat_ms = statistics.mean(x[0] for x in bat)
+    tun_ms = statistics.mean(x[0] for x in tun)
+    out = {"metric": "C3 batched build of 256 uneven graphs (t=16): total build s",
+           "value": round(tun_ms / 1e3, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(tun_ms, 3), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "config": {"workload": "256 graphs: 128 Barabasi-Albert (n log-uniform 1k-50k, m 2-8), "
+                                  "128 Watts-Strogatz (n log-uniform 1k-50k, k=6, p=0.1), seed 4",
+                      "vertices": int(start[-1]), "arcs": int(col.shape[0]), "t": t},
+           "plain_sequential_s": round(seq_ms / 1e3, 6),
+           "batched_default_s": round(bat_ms / 1e3, 6),
+           "batched_tuned_s": round(tun_ms / 1e3, 6),
+           "speedup_vs_sequential": round(seq_ms / tun_ms, 2),
+           "autotune": {"root_batch": rb, "block": bl, "wall_ms": round(tune_ms_wall, 1)},
+           "label_entries": int(seq[0][1])}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_baseline(args, scale=None):
     """The oracle as it stands (single thread) on a bounded sample: a full
@@ -423,7 +502,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256"], default="rmat20")
     ap.add_argument("--root-batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--latency-samples", type=int, default=2000)
@@ -434,6 +513,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "batch256":
+        ws, rank, local = dist_setup()
+        run_batch(args, ws, rank, local)
+        return
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup() if args.impl == "ours" else (
         int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)

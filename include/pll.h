@@ -77,7 +77,7 @@ typedef struct pll_build_opts {
 
 typedef struct pll_stats {
     uint32_t n;                  /* vertices */
-    uint32_t t;                  /* bit-parallel roots */
+    uint32_t t;                  /* bit-parallel roots (per graph) */
     uint64_t nnz;                /* arcs */
     uint64_t label_entries;      /* sum over v of |L(v)| (normal labels) */
     uint64_t pre_cleanup;        /* entries emitted by batched pruned BFSs
@@ -104,6 +104,8 @@ typedef struct pll_stats {
     uint64_t expand_launches;
     uint64_t test_launches;
     uint64_t candidates;         /* candidates passed from expand to test */
+    uint32_t graphs;             /* graphs in the index (1 unless pll_build_batch) */
+    uint32_t reserved32;
 } pll_stats;
 
 /*
@@ -135,6 +137,41 @@ PLL_API int pll_build(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
 PLL_API int pll_build_host(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
                            uint64_t nnz, const uint32_t *order, const pll_build_opts *opts,
                            void *stream, pll_index **out);
+
+/*
+ * pll_build_batch -- build the indices of several graphs in one call, as one
+ * index over their disjoint union. Graph g owns the vertex ids
+ * [graph_start[g], graph_start[g + 1]) of the union CSR (offsets, cols: device,
+ * same rules as pll_build; no arc may join two graphs, else PLL_E_INVAL).
+ * graph_start is a HOST uint32[graphs + 1] with graph_start[0] = 0 and
+ * graph_start[graphs] = n.
+ *
+ * Each graph keeps its own Degree order (Sec. 4.4.2, ties by id) and its own
+ * t bit-parallel roots chosen inside it (Sec. 5.4), so its labels and
+ * bit-parallel labels are exactly those pll_build gives for that graph alone,
+ * with hub ranks counted in the union's order (graphs interleaved by their
+ * own ranks: all rank-0 vertices first, then all rank-1 vertices, ...);
+ * pll_export_order gives that order. Bit-parallel slot i of a vertex refers to
+ * its own graph's i-th root (pll_export_bp_roots then returns graphs * t
+ * roots, graph-major). The small graphs' pruned BFSs share the GPU's sweeps.
+ * Queries across graphs answer 255. Synchronous.
+ */
+PLL_API int pll_build_batch(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                            const uint32_t *graph_start, uint32_t graphs,
+                            const pll_build_opts *opts, void *stream, pll_index **out);
+
+/*
+ * pll_autotune -- pick the pruned-stage batch size and block shape for a
+ * graph (or, with graph_start, a batch of graphs as for pll_build_batch) by
+ * timing trial builds: root_batch in {1024, 2048, 4096, 8192, 16384} at block
+ * 256, then block in {128, 512} at the best root_batch (7 builds, CUDA-event
+ * timed on the stream). Writes the fastest options (t included) to *best and
+ * their build time to *best_ms (may be NULL). The labels are the same for
+ * every choice; only the time differs. Synchronous.
+ */
+PLL_API int pll_autotune(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                         const uint32_t *graph_start, uint32_t graphs, uint32_t t, void *stream,
+                         pll_build_opts *best, double *best_ms);
 
 /*
  * pll_query -- out[i] = d_G(src[i], dst[i]) for i < q: the minimum of the
@@ -174,8 +211,9 @@ PLL_API int pll_query_host(const pll_index *idx, const uint32_t *src, const uint
  * pll_export_bp: vertex-major [n][t] arrays of L_BP (Sec. 5.1): d[v*t + i] =
  *   d_G(r_i, v) (255 if unreachable), m1 = S^{-1}_{r_i}(v), m0 = S^0_{r_i}(v)
  *   as 64-bit sets over S_{r_i} (bit j = j-th member in rank order).
- * pll_export_bp_roots: roots[t] (vertex ids; 0xFFFFFFFF = empty slot),
- *   cnt[t] = |S_{r_i}|, S[t * 64] = members of S_{r_i} (vertex ids).
+ * pll_export_bp_roots: roots[G * t] (vertex ids; 0xFFFFFFFF = empty slot),
+ *   cnt[G * t] = |S_{r_i}|, S[G * t * 64] = members of S_{r_i} (vertex ids);
+ *   G = 1 for pll_build, the number of graphs for pll_build_batch.
  * pll_export_order: order[n], order[r] = vertex of rank r.
  */
 PLL_API int pll_label_entries(const pll_index *idx, uint64_t *total);

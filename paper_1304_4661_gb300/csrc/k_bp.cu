@@ -37,15 +37,17 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t CHUNK = 256;
 
+// one block per (graph, slot): root slot q = g * t + i seeds slot i; the
+// graphs of a batch are disjoint, so their slot-i BFSs run as one sweep
 __global__ void k_bp_seed(uint32_t t, uint32_t tp, const uint32_t *__restrict__ root,
                           const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ S,
                           uint8_t *bp_d, uint64_t *bp_m) {
-    const uint32_t i = blockIdx.x, j = threadIdx.x;
-    const uint32_t r = root[i];
+    const uint32_t q = blockIdx.x, i = q % t, j = threadIdx.x;
+    const uint32_t r = root[q];
     if (r == NONE) return;
     if (j == 0) bp_d[(size_t)r * tp + i] = 0;
-    if (j < cnt[i]) {
-        uint32_t v = S[(size_t)i * BPW + j];
+    if (j < cnt[q]) {
+        uint32_t v = S[(size_t)q * BPW + j];
         bp_d[(size_t)v * tp + i] = 1;
         bp_m[2 * ((size_t)v * t + i)] = 1ull << j;  // S^{-1}(v) = {v}
     }
@@ -199,7 +201,7 @@ __global__ void k_bp_finish(size_t nt, ulonglong2 *m) {
 
 }  // namespace
 
-int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
+int bp_run(uint32_t n, uint32_t t, uint32_t graphs, const uint32_t *d_roff, const uint32_t *d_rcol,
            const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S, uint8_t *d_bp_d,
            uint64_t *d_bp_m, uint32_t *d_err, cudaStream_t s, uint32_t *levels) {
     *levels = 0;
@@ -209,7 +211,7 @@ int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rco
     const uint32_t tp = bp_stride(t);
     PLL_TRY(cudaMemsetAsync(d_bp_d, 0xff, (size_t)n * tp, s));
     PLL_TRY(cudaMemsetAsync(d_bp_m, 0, nt * 16, s));
-    k_bp_seed<<<t, BPW, 0, s>>>(t, tp, d_root, d_cnt, d_S, d_bp_d, d_bp_m);
+    k_bp_seed<<<t * graphs, BPW, 0, s>>>(t, tp, d_root, d_cnt, d_S, d_bp_d, d_bp_m);
     PLL_TRY(cudaGetLastError());
 
     // work items: (vertex, chunk of <= CHUNK arcs)

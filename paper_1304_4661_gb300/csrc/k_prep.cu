@@ -9,6 +9,8 @@
 //                ascending, so "lowest rank" == "highest priority"
 //   BP roots     Sec. 5.4: r = highest-priority unused vertex, S_r = up to 64
 //                highest-priority unused neighbours of r, bit j = j-th chosen
+#include <algorithm>
+
 #include <cub/cub.cuh>
 
 #include "pll_internal.cuh"
@@ -159,6 +161,104 @@ __global__ void k_select_bp(uint32_t n, uint32_t t, const uint32_t *__restrict__
     }
 }
 
+// ---- several graphs built as one disjoint union (pll_build_batch)
+
+// graph id of every vertex; graph g owns vertices [gs[g], gs[g+1])
+__global__ void k_graph_of(uint32_t G, const uint32_t *__restrict__ gs, uint32_t *gof) {
+    for (uint32_t g = blockIdx.x; g < G; g += gridDim.x)
+        for (uint32_t v = gs[g] + threadIdx.x; v < gs[g + 1]; v += blockDim.x) gof[v] = g;
+}
+
+// every arc stays inside its graph
+__global__ void k_check_graph_arcs(uint32_t n, const uint32_t *__restrict__ off,
+                                   const uint32_t *__restrict__ col,
+                                   const uint32_t *__restrict__ gof, uint32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const uint32_t g = gof[v];
+        for (uint32_t x = off[v] + lane; x < off[v + 1]; x += 32)
+            if (gof[col[x]] != g) atomicOr(err, ERR_CSR);
+    }
+}
+
+// first key: (graph, descending degree); a stable sort keeps ascending ids
+__global__ void k_batch_keys1(uint32_t n, const uint32_t *__restrict__ off,
+                              const uint32_t *__restrict__ gof, uint64_t *keys, uint32_t *vals) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        keys[v] = ((uint64_t)gof[v] << 32) | (0xffffffffu - (off[v + 1] - off[v]));
+        vals[v] = v;
+    }
+}
+
+// second key: (rank inside the graph, graph): graphs interleave by local rank
+__global__ void k_batch_keys2(uint32_t n, const uint32_t *__restrict__ gs,
+                              const uint32_t *__restrict__ gof, const uint32_t *__restrict__ local_order,
+                              uint64_t *keys, uint32_t *vals) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t v = local_order[p], g = gof[v];
+        keys[p] = ((uint64_t)(p - gs[g]) << 24) | g;
+        vals[p] = v;
+    }
+}
+
+// Sec. 5.4 greedy choice inside each graph, one warp per graph. local_order
+// lists each graph's vertices by its own rank; rcol is in global rank space,
+// which orders every neighbour list by the graph's own rank too.
+__global__ void k_select_bp_graphs(uint32_t G, uint32_t t, const uint32_t *__restrict__ gs,
+                                   const uint32_t *__restrict__ local_order,
+                                   const uint32_t *__restrict__ inv,
+                                   const uint32_t *__restrict__ roff,
+                                   const uint32_t *__restrict__ rcol, uint8_t *inX, uint32_t *root,
+                                   uint32_t *cnt, uint32_t *S) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += warps) {
+        const uint32_t e = gs[g + 1];
+        uint32_t next = gs[g];
+        for (uint32_t i = 0; i < t; ++i) {
+            const size_t slot = (size_t)g * t + i;
+            uint32_t r = NONE;
+            while (next < e) {
+                const uint32_t p = next + lane;
+                const uint32_t rp = p < e ? inv[local_order[p]] : NONE;
+                const bool ok = p < e && !inX[rp];
+                const unsigned m = __ballot_sync(FULL, ok);
+                if (m) {
+                    const int l = __ffs(m) - 1;
+                    r = __shfl_sync(FULL, rp, l);
+                    next = next + l + 1;
+                    break;
+                }
+                next += 32;
+            }
+            if (r == NONE) {
+                if (lane == 0) { root[slot] = NONE; cnt[slot] = 0; }
+                continue;
+            }
+            if (lane == 0) { inX[r] = 1; root[slot] = r; }
+            __syncwarp();
+            uint32_t c = 0;
+            const uint32_t b = roff[r], ee = roff[r + 1];
+            for (uint32_t x = b; x < ee && c < BPW; x += 32) {
+                const uint32_t w = (x + lane < ee) ? rcol[x + lane] : NONE;
+                const bool ok = (w != NONE) && !inX[w];
+                const unsigned m = __ballot_sync(FULL, ok);
+                const uint32_t pos = c + __popc(m & ((1u << lane) - 1u));
+                __syncwarp();
+                if (ok && pos < BPW) {
+                    S[slot * BPW + pos] = w;
+                    inX[w] = 1;
+                }
+                c += __popc(m);
+                __syncwarp();
+            }
+            if (lane == 0) cnt[slot] = c < BPW ? c : BPW;
+            __syncwarp();
+        }
+    }
+}
+
 inline int grid_for(uint64_t items, int block, int per_thread = 1) {
     uint64_t g = (items + (uint64_t)block * per_thread - 1) / ((uint64_t)block * per_thread);
     if (g < 1) g = 1;
@@ -252,6 +352,52 @@ int prep_select_bp_roots(uint32_t n, uint32_t t, const uint32_t *d_roff, const u
                          cudaStream_t s) {
     if (t == 0) return PLL_OK;
     k_select_bp<<<1, 32, 0, s>>>(n, t, d_roff, d_rcol, d_inX, d_root, d_cnt, d_S);
+    PLL_TRY(cudaGetLastError());
+    return PLL_OK;
+}
+
+}  // namespace pll
+
+namespace pll {
+
+int prep_batch_order(const Graph &g, const uint32_t *d_gs, uint32_t G, uint32_t *d_gof,
+                     uint32_t *d_local_order, uint32_t *d_order, uint32_t *d_err, cudaStream_t s) {
+    if (g.n == 0) return PLL_OK;
+    k_graph_of<<<(int)std::min<uint32_t>(G, 65535), 256, 0, s>>>(G, d_gs, d_gof);
+    k_check_graph_arcs<<<grid_for((uint64_t)g.n * 32, 256), 256, 0, s>>>(g.n, g.off, g.col, d_gof, d_err);
+    DevMem k1, k1s, v1, k2, temp;
+    PLL_CHECK(k1.alloc((size_t)g.n * 8));
+    PLL_CHECK(k1s.alloc((size_t)g.n * 8));
+    PLL_CHECK(v1.alloc((size_t)g.n * 4));
+    k_batch_keys1<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.off, d_gof, k1.as<uint64_t>(), v1.as<uint32_t>());
+    PLL_TRY(cudaGetLastError());
+    size_t tb = 0;
+    PLL_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, k1.as<uint64_t>(), k1s.as<uint64_t>(),
+                                            v1.as<uint32_t>(), d_local_order, (int)g.n, 0, 64, s));
+    PLL_CHECK(temp.alloc(tb));
+    PLL_TRY(cub::DeviceRadixSort::SortPairs(temp.p, tb, k1.as<uint64_t>(), k1s.as<uint64_t>(),
+                                            v1.as<uint32_t>(), d_local_order, (int)g.n, 0, 64, s));
+    k_batch_keys2<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, d_gs, d_gof, d_local_order,
+                                                     k1.as<uint64_t>(), v1.as<uint32_t>());
+    PLL_TRY(cudaGetLastError());
+    size_t tb2 = 0;
+    PLL_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb2, k1.as<uint64_t>(), k1s.as<uint64_t>(),
+                                            v1.as<uint32_t>(), d_order, (int)g.n, 0, 48, s));
+    if (tb2 > temp.bytes) PLL_CHECK(temp.alloc(tb2));
+    PLL_TRY(cub::DeviceRadixSort::SortPairs(temp.p, tb2, k1.as<uint64_t>(), k1s.as<uint64_t>(),
+                                            v1.as<uint32_t>(), d_order, (int)g.n, 0, 48, s));
+    PLL_TRY(cudaStreamSynchronize(s));
+    return PLL_OK;
+}
+
+int prep_select_bp_graphs(uint32_t G, uint32_t t, const uint32_t *d_gs, const uint32_t *d_local_order,
+                          const uint32_t *d_inv, const uint32_t *d_roff, const uint32_t *d_rcol,
+                          uint8_t *d_inX, uint32_t *d_root, uint32_t *d_cnt, uint32_t *d_S,
+                          cudaStream_t s) {
+    if (t == 0 || G == 0) return PLL_OK;
+    const int grid = (int)std::min<uint64_t>(((uint64_t)G * 32 + 255) / 256, 65535);
+    k_select_bp_graphs<<<grid, 256, 0, s>>>(G, t, d_gs, d_local_order, d_inv, d_roff, d_rcol, d_inX,
+                                            d_root, d_cnt, d_S);
     PLL_TRY(cudaGetLastError());
     return PLL_OK;
 }

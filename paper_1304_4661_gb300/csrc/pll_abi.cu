@@ -314,9 +314,11 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     return PLL_OK;
 }
 
+// graph_start: null for one graph; else host uint32[graphs + 1] vertex ranges
+// of graphs built together as one disjoint union.
 int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t nnz,
-                 const uint32_t *order, const pll_build_opts *opts, cudaStream_t s,
-                 pll_index **out) {
+                 const uint32_t *order, const uint32_t *graph_start, uint32_t graphs,
+                 const pll_build_opts *opts, cudaStream_t s, pll_index **out) {
     pll_build_opts o{};
     if (opts) o = *opts;
     if (!out) return PLL_E_INVAL;
@@ -331,6 +333,14 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (block != 128 && block != 256 && block != 512 && block != 1024) return PLL_E_INVAL;
     uint32_t bmax = o.root_batch ? o.root_batch : 4096;
     if (bmax > (1u << 16)) bmax = 1u << 16;
+    const bool batch = graph_start != nullptr;
+    if (!batch) graphs = 1;
+    if (batch) {
+        if (graphs == 0 || graphs > MAX_N || order) return PLL_E_INVAL;
+        if (graph_start[0] != 0 || graph_start[graphs] != n) return PLL_E_INVAL;
+        for (uint32_t gi = 0; gi < graphs; ++gi)
+            if (graph_start[gi] > graph_start[gi + 1]) return PLL_E_INVAL;
+    }
 
     pll_index *ix = new (std::nothrow) pll_index();
     if (!ix) return PLL_E_NOMEM;
@@ -342,6 +352,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     ix->n = n;
     ix->t = o.t;
     ix->tp = bp_stride(o.t);
+    ix->graphs = graphs;
     ix->nnz = nnz;
     ix->stats.n = n;
     ix->stats.t = o.t;
@@ -362,7 +373,17 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (h_err) return PLL_E_INVAL;
     PLL_TRY(cudaMalloc(&ix->d_order, std::max<size_t>((size_t)n * 4, 4)));
     PLL_TRY(cudaMalloc(&ix->d_inv, std::max<size_t>((size_t)n * 4, 4)));
-    if (order) {
+    DevMem m_gs, m_gof, m_local;
+    if (batch) {  // each graph's own Degree order, graphs interleaved by local rank
+        PLL_CHECK(m_gs.alloc(((size_t)graphs + 1) * 4));
+        PLL_CHECK(m_gof.alloc(std::max<size_t>((size_t)n * 4, 4)));
+        PLL_CHECK(m_local.alloc(std::max<size_t>((size_t)n * 4, 4)));
+        PLL_TRY(cudaMemcpyAsync(m_gs.p, graph_start, ((size_t)graphs + 1) * 4, cudaMemcpyHostToDevice, s));
+        PLL_CHECK(prep_batch_order(g, m_gs.as<uint32_t>(), graphs, m_gof.as<uint32_t>(),
+                                   m_local.as<uint32_t>(), ix->d_order, d_err, s));
+        PLL_CHECK(read_err(d_err, s, &h_err));
+        if (h_err) return PLL_E_INVAL;  // an arc joins two graphs
+    } else if (order) {
         if (n) PLL_TRY(cudaMemcpyAsync(ix->d_order, order, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
         PLL_CHECK(prep_check_order(g, ix->d_order, d_err, s));
         PLL_CHECK(read_err(d_err, s, &h_err));
@@ -377,12 +398,19 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_CHECK(m_inX.alloc(std::max<size_t>(n, 1)));
     PLL_TRY(cudaMemsetAsync(m_inX.p, 0, std::max<size_t>(n, 1), s));
     const uint32_t t = o.t;
-    PLL_TRY(cudaMalloc(&ix->d_bp_root, std::max<size_t>(t, 1) * 4));
-    PLL_TRY(cudaMalloc(&ix->d_bp_cnt, std::max<size_t>(t, 1) * 4));
-    PLL_TRY(cudaMalloc(&ix->d_bp_S, std::max<size_t>((size_t)t * BPW, 1) * 4));
-    PLL_TRY(cudaMemsetAsync(ix->d_bp_S, 0xff, std::max<size_t>((size_t)t * BPW, 1) * 4, s));
-    PLL_CHECK(prep_select_bp_roots(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(),
-                                   m_inX.as<uint8_t>(), ix->d_bp_root, ix->d_bp_cnt, ix->d_bp_S, s));
+    const size_t gt = (size_t)graphs * t;
+    PLL_TRY(cudaMalloc(&ix->d_bp_root, std::max<size_t>(gt, 1) * 4));
+    PLL_TRY(cudaMalloc(&ix->d_bp_cnt, std::max<size_t>(gt, 1) * 4));
+    PLL_TRY(cudaMalloc(&ix->d_bp_S, std::max<size_t>(gt * BPW, 1) * 4));
+    PLL_TRY(cudaMemsetAsync(ix->d_bp_S, 0xff, std::max<size_t>(gt * BPW, 1) * 4, s));
+    if (batch)
+        PLL_CHECK(prep_select_bp_graphs(graphs, t, m_gs.as<uint32_t>(), m_local.as<uint32_t>(),
+                                        ix->d_inv, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(),
+                                        m_inX.as<uint8_t>(), ix->d_bp_root, ix->d_bp_cnt,
+                                        ix->d_bp_S, s));
+    else
+        PLL_CHECK(prep_select_bp_roots(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(),
+                                       m_inX.as<uint8_t>(), ix->d_bp_root, ix->d_bp_cnt, ix->d_bp_S, s));
     if (n) {
         ix->stats.launches += (nnz ? 2 : 1) + 2 + (nnz ? 3 : 2) + (t ? 1 : 0);
         ix->stats.cub_calls += (order ? 0 : 1) + 1 + (nnz ? 1 : 0);
@@ -395,7 +423,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaMalloc(&ix->d_bp_d, std::max<size_t>((size_t)n * ix->tp, 16)));
     PLL_TRY(cudaMalloc(&ix->d_bp_m, std::max<size_t>(nt, 1) * 16));
     uint32_t bp_levels = 0;
-    PLL_CHECK(bp_run(n, t, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), ix->d_bp_root,
+    PLL_CHECK(bp_run(n, t, graphs, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), ix->d_bp_root,
                      ix->d_bp_cnt, ix->d_bp_S, ix->d_bp_d, ix->d_bp_m, d_err, s, &bp_levels));
     if (t && n) {
         ix->stats.launches += 4 + 2ull * bp_levels;  // seed, chunk counts/fill, passes, finish
@@ -414,8 +442,9 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaMalloc(&ix->d_qerr, 16));
     PLL_TRY(cudaMemsetAsync(ix->d_qerr, 0, 16, s));
     PLL_TRY(cudaStreamSynchronize(s));
-    ix->stats.index_bytes = (uint64_t)n * 8 + (uint64_t)n * ix->tp + nt * 16 + ((uint64_t)n + 1) * 8 + ix->entries * 4 +
-                            (uint64_t)t * (BPW + 2) * 4;
+    ix->stats.index_bytes = (uint64_t)n * 8 + (uint64_t)n * ix->tp + nt * 16 + ((uint64_t)n + 1) * 8 +
+                            ix->entries * 4 + gt * (BPW + 2) * 4;
+    ix->stats.graphs = graphs;
     *out = ix;
     guard.ix = nullptr;
     return PLL_OK;
@@ -467,7 +496,7 @@ PLL_API const char *pll_status_str(int status) {
 PLL_API int pll_build(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
                       const uint32_t *order, const pll_build_opts *opts, void *stream,
                       pll_index **out) {
-    return build_device(offsets, cols, n, nnz, order, opts, (cudaStream_t)stream, out);
+    return build_device(offsets, cols, n, nnz, order, nullptr, 1, opts, (cudaStream_t)stream, out);
 }
 
 PLL_API int pll_build_host(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
@@ -493,10 +522,60 @@ PLL_API int pll_build_host(const uint32_t *offsets, const uint32_t *cols, uint32
             if (n) PLL_TRY(cudaMemcpyAsync(dord.p, order, (size_t)n * 4, cudaMemcpyHostToDevice, s));
         }
         st = build_device((const uint32_t *)doff.p, (const uint32_t *)dcol.p, n, nnz,
-                          order ? (const uint32_t *)dord.p : nullptr, opts, s, out);
+                          order ? (const uint32_t *)dord.p : nullptr, nullptr, 1, opts, s, out);
     }
     if (st == PLL_OK) PLL_TRY(cudaStreamSynchronize(s));
     return st;
+}
+
+PLL_API int pll_build_batch(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                            const uint32_t *graph_start, uint32_t graphs,
+                            const pll_build_opts *opts, void *stream, pll_index **out) {
+    if (!graph_start) return PLL_E_INVAL;
+    return build_device(offsets, cols, n, nnz, nullptr, graph_start, graphs, opts,
+                        (cudaStream_t)stream, out);
+}
+
+PLL_API int pll_autotune(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                         const uint32_t *graph_start, uint32_t graphs, uint32_t t, void *stream,
+                         pll_build_opts *best, double *best_ms) {
+    if (!best) return PLL_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PLL_TRY(cudaEventCreate(&e0));
+    PLL_TRY(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev{e0, e1};
+    double best_t = 1e30;
+    pll_build_opts bo{};
+    auto trial = [&](uint32_t rb, uint32_t block) -> int {
+        pll_build_opts o{};
+        o.t = t;
+        o.root_batch = rb;
+        o.block = block;
+        pll_index *ix = nullptr;
+        PLL_TRY(cudaEventRecord(e0, s));
+        const int st = build_device(offsets, cols, n, nnz, nullptr, graph_start, graphs, &o, s, &ix);
+        if (st != PLL_OK) return st;
+        PLL_TRY(cudaEventRecord(e1, s));
+        PLL_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        PLL_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        free_index(ix);
+        if (ms < best_t) { best_t = ms; bo = o; }
+        return PLL_OK;
+    };
+    // root-batch sizes at the default block, then block shapes at the best size
+    static const uint32_t batches[] = {1024, 2048, 4096, 8192, 16384};
+    for (uint32_t rb : batches) PLL_CHECK(trial(rb, 256));
+    const uint32_t rb = bo.root_batch;
+    static const uint32_t blocks[] = {128, 512};
+    for (uint32_t bl : blocks) PLL_CHECK(trial(rb, bl));
+    *best = bo;
+    if (best_ms) *best_ms = best_t;
+    return PLL_OK;
 }
 
 PLL_API int pll_query_async(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
@@ -607,20 +686,21 @@ PLL_API int pll_export_bp(const pll_index *idx, uint8_t *d, uint64_t *m1, uint64
 PLL_API int pll_export_bp_roots(const pll_index *idx, uint32_t *roots, uint32_t *cnt, uint32_t *S) {
     if (!idx) return PLL_E_INVAL;
     const uint32_t t = idx->t, n = idx->n;
+    const size_t gt = (size_t)idx->graphs * t;
     if (t == 0) return PLL_OK;
     if (!roots || !cnt || !S) return PLL_E_INVAL;
     std::vector<uint32_t> order(n);
-    std::vector<uint32_t> hr(t), hc(t), hs((size_t)t * BPW);
+    std::vector<uint32_t> hr(gt), hc(gt), hs(gt * BPW);
     if (n) PLL_TRY(cudaMemcpy(order.data(), idx->d_order, (size_t)n * 4, cudaMemcpyDeviceToHost));
-    PLL_TRY(cudaMemcpy(hr.data(), idx->d_bp_root, (size_t)t * 4, cudaMemcpyDeviceToHost));
-    PLL_TRY(cudaMemcpy(hc.data(), idx->d_bp_cnt, (size_t)t * 4, cudaMemcpyDeviceToHost));
-    PLL_TRY(cudaMemcpy(hs.data(), idx->d_bp_S, (size_t)t * BPW * 4, cudaMemcpyDeviceToHost));
-    for (uint32_t i = 0; i < t; ++i) {
-        roots[i] = hr[i] == NONE ? NONE : order[hr[i]];
-        cnt[i] = hc[i];
+    PLL_TRY(cudaMemcpy(hr.data(), idx->d_bp_root, gt * 4, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hc.data(), idx->d_bp_cnt, gt * 4, cudaMemcpyDeviceToHost));
+    PLL_TRY(cudaMemcpy(hs.data(), idx->d_bp_S, gt * BPW * 4, cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < gt; ++q) {
+        roots[q] = hr[q] == NONE ? NONE : order[hr[q]];
+        cnt[q] = hc[q];
         for (uint32_t j = 0; j < BPW; ++j) {
-            const uint32_t r = hs[(size_t)i * BPW + j];
-            S[(size_t)i * BPW + j] = (j < hc[i] && r != NONE) ? order[r] : NONE;
+            const uint32_t r = hs[q * BPW + j];
+            S[q * BPW + j] = (j < hc[q] && r != NONE) ? order[r] : NONE;
         }
     }
     return PLL_OK;

@@ -56,14 +56,15 @@ struct pll_index {
     int device = 0;
     uint32_t n = 0, t = 0;
     uint32_t tp = 0;               // bp_d row stride: t rounded up to 16
+    uint32_t graphs = 1;           // graphs built together (disjoint union)
     uint64_t nnz = 0;
     uint32_t *d_order = nullptr;   // rank -> caller vertex id
     uint32_t *d_inv = nullptr;     // caller vertex id -> rank
     uint8_t *d_bp_d = nullptr;     // [n][tp]
     uint64_t *d_bp_m = nullptr;    // [n][t][2]
-    uint32_t *d_bp_root = nullptr; // [t] ranks (NONE = empty slot)
-    uint32_t *d_bp_cnt = nullptr;  // [t]
-    uint32_t *d_bp_S = nullptr;    // [t][64] ranks
+    uint32_t *d_bp_root = nullptr; // [graphs][t] ranks (NONE = empty slot)
+    uint32_t *d_bp_cnt = nullptr;  // [graphs][t]
+    uint32_t *d_bp_S = nullptr;    // [graphs][t][64] ranks
     uint64_t *d_lab_off = nullptr; // [n+1]
     uint32_t *d_lab = nullptr;     // packed entries
     uint64_t entries = 0;
@@ -130,10 +131,17 @@ int prep_relabel(const Graph &g, const uint32_t *d_order, uint32_t *d_inv, uint3
 int prep_select_bp_roots(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
                          uint8_t *d_inX, uint32_t *d_root, uint32_t *d_cnt, uint32_t *d_S,
                          cudaStream_t s);
+// several graphs as one disjoint union: d_gs[G+1] device vertex ranges
+int prep_batch_order(const Graph &g, const uint32_t *d_gs, uint32_t G, uint32_t *d_gof,
+                     uint32_t *d_local_order, uint32_t *d_order, uint32_t *d_err, cudaStream_t s);
+int prep_select_bp_graphs(uint32_t G, uint32_t t, const uint32_t *d_gs, const uint32_t *d_local_order,
+                          const uint32_t *d_inv, const uint32_t *d_roff, const uint32_t *d_rcol,
+                          uint8_t *d_inX, uint32_t *d_root, uint32_t *d_cnt, uint32_t *d_S,
+                          cudaStream_t s);
 
 // k_bp.cu
 inline uint32_t bp_stride(uint32_t t) { return (t + 15u) & ~15u; }
-int bp_run(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_rcol,
+int bp_run(uint32_t n, uint32_t t, uint32_t graphs, const uint32_t *d_roff, const uint32_t *d_rcol,
            const uint32_t *d_root, const uint32_t *d_cnt, const uint32_t *d_S, uint8_t *d_bp_d,
            uint64_t *d_bp_m, uint32_t *d_err, cudaStream_t s, uint32_t *levels);
 

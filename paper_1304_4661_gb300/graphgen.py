@@ -155,3 +155,21 @@ def make(spec) -> Graph:
     if kind == "ws":
         return ws(n, param, 0.1, seed)
     raise ValueError(kind)
+
+
+def union(graphs):
+    """Disjoint union of graphs as one CSR: graph g gets the vertex ids
+    [start[g], start[g+1]). Returns (offsets, cols, start) as uint32 arrays."""
+    sizes = np.array([g.n for g in graphs], dtype=np.int64)
+    start = np.zeros(len(graphs) + 1, dtype=np.int64)
+    start[1:] = np.cumsum(sizes)
+    n = int(start[-1])
+    arcs = np.array([g.nnz for g in graphs], dtype=np.int64)
+    astart = np.zeros(len(graphs) + 1, dtype=np.int64)
+    astart[1:] = np.cumsum(arcs)
+    off = np.zeros(n + 1, dtype=np.int64)
+    col = np.empty(int(astart[-1]), dtype=np.uint32)
+    for i, g in enumerate(graphs):
+        off[start[i]:start[i + 1] + 1] = g.offsets.astype(np.int64) + astart[i]
+        col[astart[i]:astart[i + 1]] = g.cols + np.uint32(start[i])
+    return off.astype(np.uint32), col, start.astype(np.uint32)

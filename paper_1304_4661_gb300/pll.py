@@ -24,7 +24,7 @@ SYMBOLS = [
     "pll_build", "pll_build_host", "pll_query", "pll_query_async", "pll_query_errors",
     "pll_query_host", "pll_label_entries", "pll_export_labels", "pll_export_bp",
     "pll_export_bp_roots", "pll_export_order", "pll_get_stats", "pll_free", "pll_status_str",
-    "pll_bp_labels_noalloc",
+    "pll_bp_labels_noalloc", "pll_build_batch", "pll_autotune",
 ]
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -45,7 +45,7 @@ class Stats(C.Structure):
                 ("launches", C.c_uint64), ("cub_calls", C.c_uint64),
                 ("ms_expand", C.c_double), ("ms_test", C.c_double),
                 ("expand_launches", C.c_uint64), ("test_launches", C.c_uint64),
-                ("candidates", C.c_uint64)]
+                ("candidates", C.c_uint64), ("graphs", C.c_uint32), ("reserved32", C.c_uint32)]
 
 
 class PLLError(RuntimeError):
@@ -100,6 +100,11 @@ def load(build_if_missing: bool = True):
     lib.pll_free.argtypes = [vp]
     lib.pll_status_str.restype = C.c_char_p
     lib.pll_status_str.argtypes = [i32]
+    lib.pll_autotune.restype = i32
+    lib.pll_autotune.argtypes = [vp, vp, u32, u64, vp, u32, u32, vp, C.POINTER(BuildOpts),
+                                 C.POINTER(C.c_double)]
+    lib.pll_build_batch.restype = i32
+    lib.pll_build_batch.argtypes = [vp, vp, u32, u64, vp, u32, C.POINTER(BuildOpts), vp, pp]
     lib.pll_bp_labels_noalloc.restype = i32
     lib.pll_bp_labels_noalloc.argtypes = [vp, vp, u32, u64, u32, vp, vp, vp, vp, vp, vp]
     _lib = lib
@@ -138,6 +143,22 @@ def _hptr(a, dtype):
     return a, a.ctypes.data
 
 
+def autotune(offsets, cols, t: int, graph_start=None, stream=None):
+    """pll_autotune on CUDA tensors; returns (root_batch, block, build_ms)."""
+    lib = load()
+    n = int(offsets.shape[0]) - 1
+    nnz = int(cols.shape[0])
+    gp, G = None, 0
+    if graph_start is not None:
+        gs, gp = _hptr(graph_start, np.uint32)
+        G = len(gs) - 1
+    best = BuildOpts()
+    ms = C.c_double(0)
+    _check(lib.pll_autotune(_dptr(offsets), _dptr(cols) if nnz else None, n, nnz, gp, G, t,
+                            _stream_handle(stream), C.byref(best), C.byref(ms)), "pll_autotune")
+    return int(best.root_batch), int(best.block), float(ms.value)
+
+
 def bp_labels_noalloc(rank_offsets, rank_cols, t: int, d, masks, roots, cnt, S, stream=None):
     """pll_bp_labels_noalloc on CUDA tensors (outputs preallocated by the caller):
     d uint8[n * tp] (tp = t rounded up to 16), masks uint64[n * t * 2],
@@ -163,6 +184,7 @@ class Index:
         self._h = handle
         self.n = n
         self.t = t
+        self.graphs = 1
 
     # ------------------------------------------------------------- build
     @classmethod
@@ -191,6 +213,24 @@ class Index:
                                     C.byref(out))
         _check(st, "pll_build")
         return cls(out.value, n, t)
+
+    @classmethod
+    def build_batch(cls, offsets, cols, graph_start, t: int = 0, root_batch: int = 0,
+                    block: int = 0, stream=None) -> "Index":
+        """pll_build_batch: CUDA tensors for the union CSR, graph_start as a
+        host uint32 array of graphs + 1 vertex boundaries."""
+        lib = load()
+        opts = BuildOpts(t, root_batch, block, 0, 0)
+        out = C.c_void_p()
+        n = int(offsets.shape[0]) - 1
+        nnz = int(cols.shape[0])
+        gs, gp = _hptr(graph_start, np.uint32)
+        st = lib.pll_build_batch(_dptr(offsets), _dptr(cols) if nnz else None, n, nnz, gp,
+                                 len(gs) - 1, C.byref(opts), _stream_handle(stream), C.byref(out))
+        _check(st, "pll_build_batch")
+        ix = cls(out.value, n, t)
+        ix.graphs = len(gs) - 1
+        return ix
 
     def close(self):
         if getattr(self, "_h", None):
@@ -263,13 +303,14 @@ class Index:
         return d[:k].reshape(shp), m1[:k].reshape(shp), m0[:k].reshape(shp)
 
     def bp_roots(self):
-        t = max(self.t, 1)
-        roots = np.empty(t, dtype=np.uint32)
-        cnt = np.empty(t, dtype=np.uint32)
-        S = np.empty(t * 64, dtype=np.uint32)
+        """roots, cnt [graphs * t] and S [graphs * t, 64] (graph-major)."""
+        gt = self.graphs * self.t
+        roots = np.empty(max(gt, 1), dtype=np.uint32)
+        cnt = np.empty(max(gt, 1), dtype=np.uint32)
+        S = np.empty(max(gt, 1) * 64, dtype=np.uint32)
         _check(load().pll_export_bp_roots(self._h, roots.ctypes.data, cnt.ctypes.data, S.ctypes.data),
                "pll_export_bp_roots")
-        return roots[: self.t], cnt[: self.t], S[: self.t * 64].reshape(self.t, 64)
+        return roots[:gt], cnt[:gt], S[: gt * 64].reshape(gt, 64)
 
     def order(self) -> np.ndarray:
         out = np.empty(max(self.n, 1), dtype=np.uint32)
