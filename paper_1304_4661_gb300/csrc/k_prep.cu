@@ -359,6 +359,21 @@ int prep_select_bp_roots(uint32_t n, uint32_t t, const uint32_t *d_roff, const u
 }  // namespace pll
 
 namespace pll {
+namespace {
+__global__ void k_graph_by_rank(uint32_t n, const uint32_t *__restrict__ order,
+                                const uint32_t *__restrict__ gof, uint32_t *out) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        out[r] = gof[order[r]];
+}
+}  // namespace
+
+int prep_graph_by_rank(uint32_t n, const uint32_t *d_order, const uint32_t *d_gof, uint32_t *d_out,
+                       cudaStream_t s) {
+    if (n == 0) return PLL_OK;
+    k_graph_by_rank<<<grid_for(n, 256), 256, 0, s>>>(n, d_order, d_gof, d_out);
+    PLL_TRY(cudaGetLastError());
+    return PLL_OK;
+}
 
 int prep_batch_order(const Graph &g, const uint32_t *d_gs, uint32_t G, uint32_t *d_gof,
                      uint32_t *d_local_order, uint32_t *d_order, uint32_t *d_err, cudaStream_t s) {

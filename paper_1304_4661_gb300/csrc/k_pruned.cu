@@ -51,6 +51,8 @@
 // Level boundaries live in a device descriptor advanced by a one-thread
 // kernel, so the host enqueues several levels ahead and reads back only to
 // learn that the frontier is empty; sweeps over an empty range return at once.
+#include <cub/cub.cuh>
+
 #include "pll_internal.cuh"
 
 namespace pll {
@@ -59,8 +61,17 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t HT_EMPTY = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t ht_slot(uint32_t h) {
-    return (h * 0x9E3779B1u) >> (32 - BATCH_HT_LOG);
+// Slot of hub rank h in a table of mask + 1 = 2^lg slots (lg >= 5): the top lg
+// bits of a two-multiply mix of h. Hub ranks of one graph in a batch share
+// their low bits (ranks interleave the graphs), so an unmixed product would
+// crowd them into few slots.
+__device__ __forceinline__ uint32_t ht_slot(uint32_t h, uint32_t mask) {
+    uint32_t x = h * 0x9E3779B1u;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 12;
+    const uint32_t lg = 31 - __clz(mask + 1);
+    return x >> (32 - lg);
 }
 
 // bytes 0x00/0xff -> 4 bits
@@ -109,20 +120,37 @@ __global__ void k_batch_init(BatchArgs a) {
             a.rootbits[2 * slot] = h1;
             a.rootbits[2 * slot + 1] = h01;
         }
-        // root array T as a hash table (labels longer than half the table are
-        // binary-searched instead)
-        uint32_t *ht = a.ht + (size_t)slot * BATCH_HT;
+        // root array T as a hash table of 2 x |L(v_k)| slots (very long labels,
+        // and tables past the pool's end, are binary-searched instead; the host
+        // grows the pool for the next batches)
         const uint32_t len = a.lab_len[k];
-        if (len <= BATCH_HT / 2) {
-            for (uint32_t s = lane; s < BATCH_HT; s += 32) ht[s] = HT_EMPTY;
+        const unsigned long long tb = a.ht_off[slot], te = a.ht_off[slot + 1];
+        if (te > a.ht_cap) {
+            if (lane == 0) atomicOr(&a.ctr->err, ERR_TABLE);
+        } else if (te > tb) {
+            uint32_t *ht = a.ht + tb;
+            const uint32_t mask = (uint32_t)(te - tb) - 1;
+            for (uint32_t s = lane; s <= mask; s += 32) ht[s] = HT_EMPTY;
             __syncwarp();
             const uint32_t *lab = a.pool + a.lab_off[k];
             for (uint32_t j = lane; j < len; j += 32) {
                 const uint32_t e = lab[j];
-                uint32_t s = ht_slot(entry_hub(e));
-                while (atomicCAS(&ht[s], HT_EMPTY, e) != HT_EMPTY) s = (s + 1) & (BATCH_HT - 1);
+                uint32_t s = ht_slot(entry_hub(e), mask);
+                while (atomicCAS(&ht[s], HT_EMPTY, e) != HT_EMPTY) s = (s + 1) & mask;
             }
         }
+    }
+}
+
+// table sizes of the batch's roots (0 for bit-parallel vertices)
+__global__ void k_ht_sizes(BatchArgs a, unsigned long long *sizes) {
+    for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot <= a.B; slot += gridDim.x * blockDim.x) {
+        uint32_t sz = 0;
+        if (slot < a.B) {
+            const uint32_t k = a.k0 + slot;
+            if (!a.inX[k]) sz = ht_size(a.lab_len[k]);
+        }
+        sizes[slot] = sz;
     }
 }
 
@@ -279,8 +307,10 @@ __device__ __forceinline__ bool prune_warp(const BatchArgs &a, uint32_t slot, ui
         if (__any_sync(FULL, p)) return true;
     }
     if (len == 0) return false;
-    const bool use_ht = rlen <= BATCH_HT / 2;
-    const uint32_t *ht = a.ht + (size_t)slot * BATCH_HT;
+    const unsigned long long tb = a.ht_off[slot], te = a.ht_off[slot + 1];
+    const bool use_ht = te > tb && te <= a.ht_cap;  // else the table was not built
+    const uint32_t mask = (uint32_t)(te - tb) - 1;
+    const uint32_t *ht = a.ht + tb;
     const uint32_t *rlab = a.pool + rlab_off;
     const uint32_t *lab = a.pool + lab_off;
     for (uint32_t j = 0; j < len; j += 32) {
@@ -290,12 +320,12 @@ __device__ __forceinline__ bool prune_warp(const BatchArgs &a, uint32_t slot, ui
             const uint32_t e = lab[j + lane], h = entry_hub(e);
             uint32_t tk = INF8;
             if (use_ht) {
-                uint32_t s = ht_slot(h);
+                uint32_t s = ht_slot(h, mask);
                 for (;;) {
                     const uint32_t y = ht[s];
                     if (y == HT_EMPTY) break;
                     if (entry_hub(y) == h) { tk = entry_dist(y); break; }
-                    s = (s + 1) & (BATCH_HT - 1);
+                    s = (s + 1) & mask;
                 }
             } else {
                 uint32_t lo = 0, hi = rlen;
@@ -415,7 +445,22 @@ int batch_grid(uint32_t block, int *grid) {
     return PLL_OK;
 }
 
-int batch_init(const BatchArgs &a, cudaStream_t s) {
+size_t batch_init_temp_bytes(uint32_t bmax) {
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, (unsigned long long *)nullptr,
+                                  (unsigned long long *)nullptr, (int)bmax + 1);
+    return tb;
+}
+
+// temp: CUB scratch of batch_init_temp_bytes(B) bytes followed by B + 1
+// 64-bit sizes
+int batch_init(const BatchArgs &a, void *temp, size_t temp_bytes, cudaStream_t s) {
+    unsigned long long *sizes = reinterpret_cast<unsigned long long *>(
+        static_cast<unsigned char *>(temp) + ((temp_bytes - ((size_t)a.B + 1) * 8) & ~(size_t)255));
+    const size_t cub_bytes = (size_t)((unsigned char *)sizes - (unsigned char *)temp);
+    k_ht_sizes<<<(int)((a.B + 256) / 256), 256, 0, s>>>(a, sizes);
+    size_t tb = cub_bytes;
+    PLL_TRY(cub::DeviceScan::ExclusiveSum(temp, tb, sizes, a.ht_off, (int)a.B + 1, s));
     const int g = (int)((a.B * 32ull + 255) / 256);
     k_batch_init<<<g > 0 ? g : 1, 256, 0, s>>>(a);
     k_batch_advance<<<1, 1, 0, s>>>(a, 0);

@@ -23,6 +23,7 @@ constexpr uint32_t BIG = 1u << 20;
 struct QueryArgs {
     uint32_t n, t, tp;
     const uint32_t *inv;
+    const uint32_t *graph;  // graph of each rank (batch indices), or null
     const uint8_t *bp_d;
     const uint64_t *bp_m;
     const uint64_t *lab_off;
@@ -60,6 +61,11 @@ __global__ void __launch_bounds__(256) k_query(QueryArgs a) {
         const uint32_t s = a.inv[sid], t = a.inv[tid];
         if (s == t) {
             if (lane == 0) a.out[qi] = 0;
+            continue;
+        }
+        // graphs of a batch share slot numbers but not roots: no distance across
+        if (a.graph && a.graph[s] != a.graph[t]) {
+            if (lane == 0) a.out[qi] = INF8;
             continue;
         }
         // bit-parallel distances: d~ per lane root
@@ -133,7 +139,7 @@ int query_launch(const pll_index *ix, const uint32_t *d_src, const uint32_t *d_d
     uint64_t want = (q * 32 + 255) / 256;
     uint64_t cap = (uint64_t)sms * per;
     int grid = (int)(want < cap ? want : cap);
-    QueryArgs a{ix->n, ix->t, ix->tp, ix->d_inv, ix->d_bp_d, ix->d_bp_m, ix->d_lab_off, ix->d_lab,
+    QueryArgs a{ix->n, ix->t, ix->tp, ix->d_inv, ix->d_graph, ix->d_bp_d, ix->d_bp_m, ix->d_lab_off, ix->d_lab,
                 d_src, d_dst, q, d_out, ix->d_qerr};
     k_query<<<grid, 256, 0, s>>>(a);
     PLL_TRY(cudaGetLastError());

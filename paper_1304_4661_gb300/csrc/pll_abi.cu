@@ -59,6 +59,7 @@ void free_index(pll_index *ix) {
     cudaFree(ix->d_bp_root);
     cudaFree(ix->d_bp_cnt);
     cudaFree(ix->d_bp_S);
+    cudaFree(ix->d_graph);
     cudaFree(ix->d_lab_off);
     cudaFree(ix->d_lab);
     cudaFree(ix->d_qerr);
@@ -121,9 +122,13 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     int grid[2] = {0, 0};
     PLL_CHECK(batch_grid(block, grid));
     const uint32_t wmax = (bmax + 31) / 32;
-    DevMem m_vis, m_ht, m_bits, m_cand, m_candc, m_out, m_sorted, m_keep, m_temp;
+    DevMem m_vis, m_ht, m_htoff, m_itemp, m_bits, m_cand, m_candc, m_out, m_sorted, m_keep, m_temp;
     PLL_CHECK(m_vis.alloc((size_t)n * wmax * 4));
-    PLL_CHECK(m_ht.alloc((size_t)bmax * BATCH_HT * 4));
+    uint64_t ht_cap = std::max<uint64_t>((uint64_t)bmax * 128, 1ull << 20);
+    PLL_CHECK(m_ht.alloc(ht_cap * 4));
+    PLL_CHECK(m_htoff.alloc(((size_t)bmax + 1) * 8));
+    const size_t itemp_bytes = ((batch_init_temp_bytes(bmax) + 255) & ~(size_t)255) + ((size_t)bmax + 1) * 8 + 256;
+    PLL_CHECK(m_itemp.alloc(itemp_bytes));
     PLL_CHECK(m_bits.alloc((size_t)bmax * 16));
     uint64_t cand_cap = std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
     uint64_t out_cap = std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
@@ -203,6 +208,8 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         a.k0 = k0; a.B = k1 - k0; a.W = (a.B + 31) / 32;
         a.visited = m_vis.as<uint32_t>();
         a.ht = m_ht.as<uint32_t>();
+        a.ht_off = m_htoff.as<unsigned long long>();
+        a.ht_cap = ht_cap;
         a.rootbits = m_bits.as<uint64_t>();
         a.cand = m_cand.as<uint64_t>(); a.candc = m_candc.as<uint64_t>(); a.cand_cap = cand_cap;
         a.out = m_out.as<uint64_t>(); a.out_cap = out_cap;
@@ -211,8 +218,9 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)n * a.W * 4, s));
         PLL_TRY(cudaMemsetAsync(d_ctr, 0, 16, s));  // cand_n, out_n
         PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
-        PLL_CHECK(batch_init(a, s));
-        ix->stats.launches += 2;
+        PLL_CHECK(batch_init(a, m_itemp.p, itemp_bytes, s));
+        ix->stats.launches += 3;
+        ix->stats.cub_calls += 1;
         // enqueue levels ahead; read back only to find the empty frontier.
         // Events around every expand and test sweep give their device times.
         uint32_t ahead = 4;
@@ -230,7 +238,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             }
             ix->stats.expand_launches += ahead;
             ix->stats.test_launches += ahead;
-            if (h->c.err || h->d.lvl_b == h->d.lvl_e) break;
+            if ((h->c.err & (ERR_DEPTH | ERR_BUF)) || h->d.lvl_b == h->d.lvl_e) break;
             ahead = 2;
         }
         PLL_TRY(cudaEventRecord(ev1, s));
@@ -242,6 +250,16 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             ix->stats.pruned_launches += 1;
         }
         if (h->c.err & ERR_DEPTH) return PLL_E_RANGE;
+        if (h->c.err & ERR_TABLE) {  // some root tables did not fit: those roots were
+            // binary-searched (same answers); grow the pool for later batches
+            unsigned long long need = 0;
+            PLL_TRY(cudaMemcpyAsync(&need, m_htoff.as<unsigned long long>() + a.B, 8,
+                                    cudaMemcpyDeviceToHost, s));
+            PLL_TRY(cudaStreamSynchronize(s));
+            ht_cap = std::max<uint64_t>(need + need / 4, ht_cap * 2);
+            PLL_CHECK(m_ht.alloc(ht_cap * 4));
+            h->c.err &= ~ERR_TABLE;
+        }
         if (h->c.err & ERR_BUF) {  // a buffer overflowed: grow and redo the batch
             PLL_TRY(cudaMemcpyAsync(d_ctr->work, work0, sizeof(work0), cudaMemcpyHostToDevice, s));
             if (h->c.cand_n > cand_cap) {
@@ -403,6 +421,10 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaMalloc(&ix->d_bp_cnt, std::max<size_t>(gt, 1) * 4));
     PLL_TRY(cudaMalloc(&ix->d_bp_S, std::max<size_t>(gt * BPW, 1) * 4));
     PLL_TRY(cudaMemsetAsync(ix->d_bp_S, 0xff, std::max<size_t>(gt * BPW, 1) * 4, s));
+    if (batch) {
+        PLL_TRY(cudaMalloc(&ix->d_graph, std::max<size_t>((size_t)n * 4, 4)));
+        PLL_CHECK(prep_graph_by_rank(n, ix->d_order, m_gof.as<uint32_t>(), ix->d_graph, s));
+    }
     if (batch)
         PLL_CHECK(prep_select_bp_graphs(graphs, t, m_gs.as<uint32_t>(), m_local.as<uint32_t>(),
                                         ix->d_inv, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(),

@@ -65,6 +65,7 @@ struct pll_index {
     uint32_t *d_bp_root = nullptr; // [graphs][t] ranks (NONE = empty slot)
     uint32_t *d_bp_cnt = nullptr;  // [graphs][t]
     uint32_t *d_bp_S = nullptr;    // [graphs][t][64] ranks
+    uint32_t *d_graph = nullptr;   // [n] graph of each rank (batch indices only)
     uint64_t *d_lab_off = nullptr; // [n+1]
     uint32_t *d_lab = nullptr;     // packed entries
     uint64_t entries = 0;
@@ -134,6 +135,8 @@ int prep_select_bp_roots(uint32_t n, uint32_t t, const uint32_t *d_roff, const u
 // several graphs as one disjoint union: d_gs[G+1] device vertex ranges
 int prep_batch_order(const Graph &g, const uint32_t *d_gs, uint32_t G, uint32_t *d_gof,
                      uint32_t *d_local_order, uint32_t *d_order, uint32_t *d_err, cudaStream_t s);
+int prep_graph_by_rank(uint32_t n, const uint32_t *d_order, const uint32_t *d_gof, uint32_t *d_out,
+                       cudaStream_t s);
 int prep_select_bp_graphs(uint32_t G, uint32_t t, const uint32_t *d_gs, const uint32_t *d_local_order,
                           const uint32_t *d_inv, const uint32_t *d_roff, const uint32_t *d_rcol,
                           uint8_t *d_inX, uint32_t *d_root, uint32_t *d_cnt, uint32_t *d_S,
@@ -153,8 +156,16 @@ int bp_run_in(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_
               size_t scratch_bytes, cudaStream_t s);
 
 // k_pruned.cu -- batch-synchronous pruned BFS over roots [k0, k0 + B)
-constexpr int BATCH_HT_LOG = 9;
-constexpr uint32_t BATCH_HT = 1u << BATCH_HT_LOG;  // hash slots per root label
+// root label hash tables: 2 x |L(v_k)| slots rounded up to a power of two,
+// at least HT_MIN; labels longer than HT_MAX / 2 are binary-searched instead
+constexpr uint32_t HT_MIN = 32;
+constexpr uint32_t HT_MAX = 1u << 16;
+__host__ __device__ inline uint32_t ht_size(uint32_t len) {
+    if (len == 0 || 2 * len > HT_MAX) return 0;
+    uint32_t s = HT_MIN;
+    while (s < 2 * len) s <<= 1;
+    return s;
+}
 
 struct BatchCounters {
     unsigned long long cand_n;    // candidates appended (all levels of the batch)
@@ -166,6 +177,7 @@ struct BatchCounters {
     uint32_t err;
     uint32_t pad;
 };
+constexpr uint32_t ERR_TABLE = 1u << 5;  // root hash-table pool too small
 
 struct LevelDesc {
     unsigned long long lvl_b, lvl_e;    // entries of the current level
@@ -186,7 +198,9 @@ struct BatchArgs {
     const uint32_t *pool;
     uint32_t k0, B, W;         // roots [k0, k0 + B), W = ceil(B / 32)
     uint32_t *visited;         // [n][W] bitmap, one bit per batch root
-    uint32_t *ht;              // [B][BATCH_HT] root label hash tables
+    uint32_t *ht;              // pool of root label hash tables
+    unsigned long long *ht_off;  // [B + 1] table offsets in the pool (exclusive sums)
+    unsigned long long ht_cap;   // pool capacity (entries)
     uint64_t *rootbits;        // [B][2] feasibility masks
     uint64_t *cand;            // (slot << 32 | vertex), all levels
     uint64_t *candc;           // [cand_cap][2] roots whose masks may still prune
@@ -197,7 +211,8 @@ struct BatchArgs {
     LevelDesc *desc;
 };
 int batch_grid(uint32_t block, int *grid);  // grid[2]: expand, test
-int batch_init(const BatchArgs &a, cudaStream_t s);
+int batch_init(const BatchArgs &a, void *temp, size_t temp_bytes, cudaStream_t s);
+size_t batch_init_temp_bytes(uint32_t bmax);
 int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s,
                 cudaEvent_t *ev);
 
