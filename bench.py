@@ -439,6 +439,117 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ serving loop
+def run_serve(args, ws, rank, local):
+    """R-MAT-22 (ef 16, seed 6), t = 64, index resident in HBM, served by the
+    continuous-batching loop (pll_server_*). Requests: 90 % hold a log-uniform
+    1-4096 number of uniform pairs, 10 % are one source with 1,000 uniform
+    targets. Saturation = the whole request stream offered at once; then
+    open-loop Poisson arrivals at 0.25 / 0.5 / 0.75 / 0.9 x saturation. The
+    plain form answers the same requests one synchronous pll_query_host call
+    at a time."""
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+    g = gg.rmat(22, 16, seed=6)
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    d_off, d_col = dev(g.offsets), dev(g.cols)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = pll.Index.build(d_off, d_col, t=64)
+    build_s = time.perf_counter() - t0
+    del d_off, d_col
+    count = args.serve_requests
+    s, u, off, many = gg.serve_requests(g.n, count, seed=8)
+    off = off.astype(np.int64)
+    total = int(off[-1])
+    mean_pairs = total / count
+    sv = pll.Server(ix)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+
+    def replay(k, arrivals):
+        return sv.replay(s[: off[k]], u[: off[k]], off[: k + 1], arrivals)
+
+    for _ in range(args.warmup):
+        replay(min(count, 2000), np.zeros(min(count, 2000)))
+    clocks.start()
+    sat = []
+    for _ in range(args.steps):
+        out, lat, el = replay(count, np.zeros(count))
+        sat.append(total / (el * 1e-6))
+    qps_sat = statistics.median(sat)
+    served_out = out.copy()
+    loads = []
+    for i, frac in enumerate((0.25, 0.5, 0.75, 0.9)):
+        rate = frac * qps_sat / mean_pairs  # requests per second
+        k = min(count, max(2000, int(rate * args.serve_seconds)))
+        arr = gg.poisson_arrivals(k, rate, 9 + i)
+        b0 = sv.stats()["batches"]
+        _, lat, el = replay(k, arr)
+        nb = sv.stats()["batches"] - b0
+        loads.append({"load": frac, "offered_req_per_s": round(rate, 1), "requests": k,
+                      "queries_per_s": round(int(off[k]) / (el * 1e-6), 1),
+                      "p50_us": round(float(np.percentile(lat, 50)), 1),
+                      "p99_us": round(float(np.percentile(lat, 99)), 1),
+                      "mean_pairs_per_batch": round(int(off[k]) / max(nb, 1), 1)})
+    clk = clocks.stop()
+    st = sv.stats()
+    sv.stop()
+    # plain form: one synchronous host-pointer query call per request
+    kp = min(count, args.serve_plain)
+    plain_lat = []
+    plain_out = np.empty(int(off[kp]), dtype=np.uint8)
+    tp0 = time.perf_counter()
+    for i in range(kp):
+        a, b = int(off[i]), int(off[i + 1])
+        c0 = time.perf_counter()
+        plain_out[a:b] = ix.query(s[a:b], u[a:b])
+        plain_lat.append((time.perf_counter() - c0) * 1e6)
+    plain_el = time.perf_counter() - tp0
+    assert np.array_equal(plain_out, served_out[: int(off[kp])]), "served != plain answers"
+    entries = ix.label_entries()
+    ix.close()
+    out = {"metric": "C5 served queries/s at saturation (R-MAT-22, t=64), p50/p99 request latency "
+                     "at 0.25-0.9x load",
+           "value": round(qps_sat, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total / qps_sat * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic",
+           "config": {"workload": "R-MAT-22 (ef 16, seed 6), t=64; requests: 90% log-uniform "
+                                  "1-4096 uniform pairs, 10% one-to-1000 (seed 8)",
+                      "vertices": g.n, "arcs": g.nnz, "requests": count, "pairs": total,
+                      "server": {"pool_bytes": st["pool_bytes"], "streams": 4,
+                                 "max_batch_pairs": st["max_request_pairs"]},
+                      "l2": "request pairs are copied fresh from host memory every request"},
+           "build_s": round(build_s, 3), "label_entries": entries,
+           "saturation_queries_per_s": [round(x, 1) for x in sat],
+           "loads": loads,
+           "plain": {"form": "one synchronous pll_query_host call per request", "requests": kp,
+                     "queries_per_s": round(int(off[kp]) / plain_el, 1),
+                     "p50_us": round(float(np.percentile(plain_lat, 50)), 1),
+                     "p99_us": round(float(np.percentile(plain_lat, 99)), 1)},
+           "server_stats": st,
+           "clocks": clk,
+           "e2e": {"value": round(qps_sat, 1), "unit": "queries/s",
+                   "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": total},
+           "gpu_launches": st["batches"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_baseline(args, scale=None):
     """The oracle as it stands (single thread) on a bounded sample: a full
@@ -502,20 +613,23 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256"], default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve"], default="rmat20")
     ap.add_argument("--root-batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--latency-samples", type=int, default=2000)
     ap.add_argument("--cpu-scale", type=int, default=17)
     ap.add_argument("--ref-scale", type=int, default=15)
+    ap.add_argument("--serve-requests", type=int, default=100_000)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-plain", type=int, default=5000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload == "batch256":
+    if args.workload in ("batch256", "serve"):
         ws, rank, local = dist_setup()
-        run_batch(args, ws, rank, local)
+        (run_batch if args.workload == "batch256" else run_serve)(args, ws, rank, local)
         return
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup() if args.impl == "ours" else (

@@ -28,6 +28,7 @@ CU_SOURCES = [
     "k_labels.cu",
     "k_query.cu",
     "pll_noalloc.cu",
+    "pll_serve.cu",
 ]
 
 

@@ -173,3 +173,32 @@ def union(graphs):
         off[start[i]:start[i + 1] + 1] = g.offsets.astype(np.int64) + astart[i]
         col[astart[i]:astart[i + 1]] = g.cols + np.uint32(start[i])
     return off.astype(np.uint32), col, start.astype(np.uint32)
+
+
+def serve_requests(n: int, count: int, seed: int, one_to_many: float = 0.1, fan: int = 1000,
+                   max_pairs: int = 4096):
+    """A request mix for the serving loop: a fraction `one_to_many` of the
+    requests are one source with `fan` uniform targets, the rest hold a
+    log-uniform number of uniform pairs in [1, max_pairs]. Returns (src, dst,
+    req_off, one_to_many_mask); request i is pairs req_off[i] .. req_off[i+1]."""
+    u = uniform(seed, 2 * count)
+    many = u[:count] < one_to_many
+    sizes = np.floor(np.exp(u[count:] * math.log(max_pairs + 1))).astype(np.int64)
+    sizes = np.clip(sizes, 1, max_pairs)
+    sizes[many] = fan
+    off = np.zeros(count + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(sizes)
+    s, t = pairs(n, int(off[-1]), seed + 1)
+    req = np.repeat(np.arange(count), sizes)
+    first = s[off[:-1].astype(np.int64)]
+    s = np.where(many[req], first[req], s).astype(np.uint32)
+    return s, t, off, many
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times in microseconds of an open-loop Poisson process of the
+    given rate (exponential gaps from seeded uniforms), starting at 0."""
+    u = uniform(seed, count)
+    gaps = -np.log1p(-u) / rate_per_s * 1e6
+    out = np.cumsum(gaps)
+    return out - out[0] if count else out

@@ -25,6 +25,8 @@ SYMBOLS = [
     "pll_query_host", "pll_label_entries", "pll_export_labels", "pll_export_bp",
     "pll_export_bp_roots", "pll_export_order", "pll_get_stats", "pll_free", "pll_status_str",
     "pll_bp_labels_noalloc", "pll_build_batch", "pll_autotune",
+    "pll_server_start", "pll_server_submit", "pll_server_wait", "pll_server_replay",
+    "pll_server_get_stats", "pll_server_stop",
 ]
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -46,6 +48,17 @@ class Stats(C.Structure):
                 ("ms_expand", C.c_double), ("ms_test", C.c_double),
                 ("expand_launches", C.c_uint64), ("test_launches", C.c_uint64),
                 ("candidates", C.c_uint64), ("graphs", C.c_uint32), ("reserved32", C.c_uint32)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("pool_bytes", C.c_uint64), ("max_batch_pairs", C.c_uint64),
+                ("streams", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("requests", C.c_uint64), ("pairs", C.c_uint64), ("batches", C.c_uint64),
+                ("max_batch_pairs", C.c_uint64), ("max_inflight_bytes", C.c_uint64),
+                ("pool_bytes", C.c_uint64), ("max_request_pairs", C.c_uint64)]
 
 
 class PLLError(RuntimeError):
@@ -107,6 +120,19 @@ def load(build_if_missing: bool = True):
     lib.pll_build_batch.argtypes = [vp, vp, u32, u64, vp, u32, C.POINTER(BuildOpts), vp, pp]
     lib.pll_bp_labels_noalloc.restype = i32
     lib.pll_bp_labels_noalloc.argtypes = [vp, vp, u32, u64, u32, vp, vp, vp, vp, vp, vp]
+    dp = C.POINTER(C.c_double)
+    lib.pll_server_start.restype = i32
+    lib.pll_server_start.argtypes = [vp, C.POINTER(ServerOpts), pp]
+    lib.pll_server_submit.restype = i32
+    lib.pll_server_submit.argtypes = [vp, vp, vp, u64, vp, C.POINTER(C.c_uint64)]
+    lib.pll_server_wait.restype = i32
+    lib.pll_server_wait.argtypes = [vp, u64, C.c_int64, dp]
+    lib.pll_server_replay.restype = i32
+    lib.pll_server_replay.argtypes = [vp, vp, vp, vp, vp, u64, vp, vp, dp]
+    lib.pll_server_get_stats.restype = i32
+    lib.pll_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    lib.pll_server_stop.restype = i32
+    lib.pll_server_stop.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -321,3 +347,80 @@ class Index:
         s = Stats()
         _check(load().pll_get_stats(self._h, C.byref(s)), "pll_get_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class Server:
+    """pll_server_*: continuous-batching query service over a resident Index.
+
+    Requests are host numpy arrays; the server keeps references to them until
+    they are waited for, so callers may drop their own."""
+
+    def __init__(self, index: "Index", pool_bytes: int = 0, max_batch_pairs: int = 0,
+                 streams: int = 0):
+        self._lib = load()
+        self.index = index  # keeps the index alive while the server runs
+        o = ServerOpts(pool_bytes, max_batch_pairs, streams, 0)
+        h = C.c_void_p()
+        _check(self._lib.pll_server_start(index._h, C.byref(o), C.byref(h)), "pll_server_start")
+        self._h = h.value
+        self._live = {}
+
+    def submit(self, src, dst) -> int:
+        s, sp = _hptr(src, np.uint32)
+        d, dp = _hptr(dst, np.uint32)
+        assert s.shape == d.shape and s.ndim == 1
+        out = np.empty(max(len(s), 1), dtype=np.uint8)
+        tk = C.c_uint64(0)
+        _check(self._lib.pll_server_submit(self._h, sp, dp, len(s), out.ctypes.data,
+                                           C.byref(tk)), "pll_server_submit")
+        self._live[tk.value] = (s, d, out)
+        return tk.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """Returns (distances, latency_us) of a submitted request."""
+        lat = C.c_double(0)
+        code = self._lib.pll_server_wait(self._h, ticket, timeout_us, C.byref(lat))
+        if code == PLL_E_TIMEOUT:
+            raise TimeoutError(f"request {ticket} not done after {timeout_us} us")
+        s, _, out = self._live.pop(ticket)
+        _check(code, "pll_server_wait")
+        return out[: len(s)], float(lat.value)
+
+    def replay(self, src, dst, req_off, arrival_us):
+        """Open-loop replay; returns (out uint8[total], latency_us[count], elapsed_us)."""
+        s, sp = _hptr(src, np.uint32)
+        d, dp = _hptr(dst, np.uint32)
+        off, op = _hptr(req_off, np.uint64)
+        arr, ap = _hptr(arrival_us, np.float64)
+        count = len(off) - 1
+        assert len(arr) == count and int(off[-1]) == len(s) == len(d)
+        out = np.empty(max(len(s), 1), dtype=np.uint8)
+        lat = np.empty(max(count, 1), dtype=np.float64)
+        el = C.c_double(0)
+        _check(self._lib.pll_server_replay(self._h, sp, dp, op, ap, count, out.ctypes.data,
+                                           lat.ctypes.data, C.byref(el)), "pll_server_replay")
+        return out[: len(s)], lat[:count], float(el.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.pll_server_get_stats(self._h, C.byref(st)), "pll_server_get_stats")
+        return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            code = self._lib.pll_server_stop(h)
+            self._live.clear()
+            _check(code, "pll_server_stop")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -72,3 +72,30 @@ def test_batch_specs():
     assert sum(1 for s in specs if s[0] == "ba") == 128
     assert all(1000 <= s[1] <= 50000 for s in specs)
     assert all(2 <= s[2] <= 8 for s in specs if s[0] == "ba")
+
+
+def test_serve_request_mix():
+    n = 5000
+    s, t, off, many = gg.serve_requests(n, 2000, 11)
+    sizes = np.diff(off.astype(np.int64))
+    assert sizes.min() >= 1 and sizes.max() <= 4096
+    assert (sizes[many] == 1000).all()
+    assert 0.06 < many.mean() < 0.14
+    normal = sizes[~many]
+    # log-uniform on [1, 4096]: about half the requests below sqrt(4097) ~ 64
+    assert 0.4 < (normal < 64).mean() < 0.6
+    assert s.max() < n and t.max() < n and len(s) == len(t) == int(off[-1])
+    for i in np.flatnonzero(many)[:20]:
+        a, b = int(off[i]), int(off[i + 1])
+        assert (s[a:b] == s[a]).all()
+    s2, t2, off2, _ = gg.serve_requests(n, 2000, 11)
+    assert np.array_equal(s, s2) and np.array_equal(t, t2) and np.array_equal(off, off2)
+
+
+def test_poisson_arrivals():
+    a = gg.poisson_arrivals(20000, 1000.0, 5)
+    gaps = np.diff(a)
+    assert a[0] == 0 and (gaps >= 0).all()
+    # exponential gaps of mean 1 ms: mean and coefficient of variation near 1
+    assert abs(gaps.mean() - 1000.0) < 30
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05
