@@ -472,7 +472,23 @@ def run_serve(args, ws, rank, local):
     off = off.astype(np.int64)
     total = int(off[-1])
     mean_pairs = total / count
-    sv = pll.Server(ix)
+    # the query kernel alone over the whole request stream, device-resident pairs
+    d_s, d_u = dev(s), dev(u)
+    d_o = torch.empty(total, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    kern = []
+    for it in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.query_async(d_s, d_u, d_o)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            kern.append(e0.elapsed_time(e1))
+    assert ix.query_errors() == 0
+    kernel_qps = total / (statistics.median(kern) * 1e-3)
+    del d_s, d_u, d_o
+    sv = pll.Server(ix, streams=args.serve_streams)
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -481,15 +497,22 @@ def run_serve(args, ws, rank, local):
     clocks = ClockSampler(uuid)
 
     def replay(k, arrivals):
-        return sv.replay(s[: off[k]], u[: off[k]], off[: k + 1], arrivals)
+        return sv.replay(s[: off[k]], u[: off[k]], off[: k + 1], arrivals, threads=args.serve_clients)
 
     for _ in range(args.warmup):
         replay(min(count, 2000), np.zeros(min(count, 2000)))
     clocks.start()
     sat = []
+    ss0 = sv.stats()
     for _ in range(args.steps):
         out, lat, el = replay(count, np.zeros(count))
         sat.append(total / (el * 1e-6))
+    ss1 = sv.stats()
+    sat_detail = {k: round((ss1[k] - ss0[k]) / args.steps / 1e3, 2)
+                  for k in ("pack_us", "unpack_us", "device_us")}
+    sat_detail["batches_per_step"] = (ss1["batches"] - ss0["batches"]) / args.steps
+    sat_detail["p50_us"] = round(float(np.percentile(lat, 50)), 1)
+    sat_detail["p99_us"] = round(float(np.percentile(lat, 99)), 1)
     qps_sat = statistics.median(sat)
     served_out = out.copy()
     loads = []
@@ -497,14 +520,19 @@ def run_serve(args, ws, rank, local):
         rate = frac * qps_sat / mean_pairs  # requests per second
         k = min(count, max(2000, int(rate * args.serve_seconds)))
         arr = gg.poisson_arrivals(k, rate, 9 + i)
-        b0 = sv.stats()["batches"]
+        st0 = sv.stats()
         _, lat, el = replay(k, arr)
-        nb = sv.stats()["batches"] - b0
+        st1 = sv.stats()
+        nb = st1["batches"] - st0["batches"]
         loads.append({"load": frac, "offered_req_per_s": round(rate, 1), "requests": k,
                       "queries_per_s": round(int(off[k]) / (el * 1e-6), 1),
                       "p50_us": round(float(np.percentile(lat, 50)), 1),
                       "p99_us": round(float(np.percentile(lat, 99)), 1),
-                      "mean_pairs_per_batch": round(int(off[k]) / max(nb, 1), 1)})
+                      "mean_pairs_per_batch": round(int(off[k]) / max(nb, 1), 1),
+                      "host_pack_unpack_ms": round((st1["pack_us"] + st1["unpack_us"]
+                                                    - st0["pack_us"] - st0["unpack_us"]) / 1e3, 2),
+                      "device_stream_ms": round((st1["device_us"] - st0["device_us"]) / 1e3, 2),
+                      "wall_ms": round(el / 1e3, 2)})
     clk = clocks.stop()
     st = sv.stats()
     sv.stop()
@@ -531,11 +559,13 @@ def run_serve(args, ws, rank, local):
            "config": {"workload": "R-MAT-22 (ef 16, seed 6), t=64; requests: 90% log-uniform "
                                   "1-4096 uniform pairs, 10% one-to-1000 (seed 8)",
                       "vertices": g.n, "arcs": g.nnz, "requests": count, "pairs": total,
-                      "server": {"pool_bytes": st["pool_bytes"], "streams": 4,
+                      "server": {"pool_bytes": st["pool_bytes"], "streams": args.serve_streams, "client_threads": args.serve_clients,
                                  "max_batch_pairs": st["max_request_pairs"]},
                       "l2": "request pairs are copied fresh from host memory every request"},
            "build_s": round(build_s, 3), "label_entries": entries,
+           "kernel_only_queries_per_s": round(kernel_qps, 1),
            "saturation_queries_per_s": [round(x, 1) for x in sat],
+           "saturation_step_ms": sat_detail,
            "loads": loads,
            "plain": {"form": "one synchronous pll_query_host call per request", "requests": kp,
                      "queries_per_s": round(int(off[kp]) / plain_el, 1),
@@ -622,6 +652,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-plain", type=int, default=5000)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-clients", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -270,39 +270,47 @@ PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *
  * Sec. 1); every answer is Query(s, t) exactly as pll_query gives it.
  *
  * A request is q >= 1 pairs in HOST memory plus a HOST uint8[q] result
- * buffer; all three stay owned by the caller and must stay valid until the
- * request is waited for. One dispatcher thread per server:
- *   - admits requests in arrival order as device memory frees up: a batch
- *     of p pairs holds about 9 p bytes of a fixed pool (pool_bytes) from the
- *     moment it is launched until its results are back;
- *   - whenever one of `streams` stream slots is free, packs every admitted
- *     waiting request (up to max_batch_pairs pairs) into one query launch;
- *     requests arriving while batches run join the next batch, and batches on
- *     different slots overlap on the GPU;
- *   - completes requests in launch order, recording each latency (submit to
- *     results in the caller's buffer, host steady clock, microseconds).
+ * buffer, all owned by the caller; the pairs are read inside
+ * pll_server_submit, the result buffer must stay valid until the request is
+ * waited for. The server holds a ring of P = pool_bytes / 9 pair slots in
+ * device memory (8 bytes per pair, 1 per result), mirrored in pinned host
+ * memory:
+ *   - admission by memory: a request is admitted when q contiguous slots are
+ *     free; until then pll_server_submit blocks. Its slots are held until its
+ *     results are back, so at most P pairs are queued or in flight;
+ *   - continuous batching: one dispatcher thread launches, whenever one of
+ *     `streams` stream slots is free, every admitted request not yet launched
+ *     (arrival order, up to max_batch_pairs pairs) as one copy-in, one query
+ *     launch and one copy-out; requests that arrive while others are on the
+ *     GPU form the next launch, and launches on different stream slots
+ *     overlap on the device;
+ *   - requests complete in launch order; each latency is measured from the
+ *     start of pll_server_submit to the results being in the caller's buffer
+ *     (host steady clock, microseconds), admission wait included.
  * A result never depends on which requests it was batched with.
  *
  * pll_server_start   starts a server on idx's device. opts may be NULL;
  *                    zero fields take the defaults (pool_bytes 256 MiB,
- *                    max_batch_pairs 2^20, streams 4). max_batch_pairs is
- *                    lowered to what pool_bytes holds. The index must outlive
- *                    the server. PLL_E_INVAL for streams > 64, a pool too
- *                    small for one pair or reserved != 0; PLL_E_NOMEM if the
- *                    pool or the pinned staging cannot be allocated.
- * pll_server_submit  queues a request and returns its ticket. PLL_E_RANGE if
- *                    q exceeds the server's max_batch_pairs (stats field
- *                    max_request_pairs), PLL_E_INVAL if an id is >= n.
+ *                    max_batch_pairs 2^20, streams 4). The index must outlive
+ *                    the server. PLL_E_INVAL for streams > 64, pool_bytes < 9
+ *                    or reserved != 0; PLL_E_NOMEM if the device ring or its
+ *                    pinned mirror cannot be allocated.
+ * pll_server_submit  admits and stages a request and returns its ticket.
+ *                    PLL_E_RANGE if q exceeds min(max_batch_pairs, P) (stats
+ *                    field max_request_pairs), PLL_E_INVAL if an id is >= n
+ *                    (nothing is queued for the caller then).
  * pll_server_wait    waits for a ticket (timeout_us < 0: no limit; on
  *                    PLL_E_TIMEOUT the ticket stays valid), writes its latency
  *                    and releases the ticket. Returns the request's status.
- * pll_server_replay  an open-loop load generator: submits request i (pairs
+ * pll_server_replay  an open-loop load generator: `threads` client threads
+ *                    (0 = 1, at most 64) submit request i (pairs
  *                    src/dst[req_off[i] .. req_off[i+1]), results to the same
  *                    range of out) at arrival_us[i] microseconds after the
- *                    call starts (non-decreasing), waits for all, and writes
+ *                    call starts (non-decreasing), thread i % threads taking
+ *                    request i; it waits for all, and writes
  *                    latency_us[i] (-1 for a request not submitted after an
  *                    error) and the wall time to *elapsed_us (may be NULL).
- * pll_server_stop    finishes every queued request, stops the thread and
+ * pll_server_stop    finishes every admitted request, stops the thread and
  *                    frees the server; tickets not yet waited for are
  *                    released. No other call on the server may run during or
  *                    after it. Returns the first launch error seen, if any.
@@ -322,6 +330,10 @@ typedef struct pll_server_stats {
     uint64_t max_inflight_bytes;        /* peak pool bytes held by batches */
     uint64_t pool_bytes;                /* the pool's size */
     uint64_t max_request_pairs;         /* largest request accepted */
+    double pack_us;                     /* client time staging pairs at submit */
+    double unpack_us;                   /* dispatcher time delivering results */
+    double device_us;                   /* sum over batches of copy-in..copy-out
+                                           stream time (batches overlap) */
 } pll_server_stats;
 
 PLL_API int pll_server_start(const pll_index *idx, const pll_server_opts *opts, pll_server **out);
@@ -331,7 +343,8 @@ PLL_API int pll_server_wait(pll_server *sv, uint64_t ticket, int64_t timeout_us,
                             double *latency_us);
 PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_t *dst,
                               const uint64_t *req_off, const double *arrival_us, uint64_t count,
-                              uint8_t *out, double *latency_us, double *elapsed_us);
+                              uint32_t threads, uint8_t *out, double *latency_us,
+                              double *elapsed_us);
 PLL_API int pll_server_get_stats(pll_server *sv, pll_server_stats *out);
 PLL_API int pll_server_stop(pll_server *sv);
 

@@ -243,5 +243,8 @@ int scan_u32_to_u64(const uint32_t *d_in, uint64_t *d_out, uint32_t n, void *d_t
 // k_query.cu
 int query_launch(const pll_index *ix, const uint32_t *d_src, const uint32_t *d_dst, uint64_t q,
                  uint8_t *d_out, cudaStream_t s);
+// as query_launch with pair i at (d_src[i * stride], d_dst[i * stride])
+int query_launch_strided(const pll_index *ix, const uint32_t *d_src, const uint32_t *d_dst,
+                         uint32_t stride, uint64_t q, uint8_t *d_out, cudaStream_t s);
 
 }  // namespace pll

@@ -4,21 +4,26 @@
 // latency-sensitive services (Sec. 1); this loop serves Query(s, t) (Sec. 3.3
 // with the bit-parallel part of Sec. 5.3) for many clients at once.
 //
-// Requests (pairs in host memory) are queued by pll_server_submit. One
-// dispatcher thread runs continuous batching:
-//   * admission by memory: a batch needs 9 bytes per pair on the device
-//     (source, target, result, each block 256-byte aligned); it is admitted
-//     when that fits in the free part of a FIFO ring over a fixed device
-//     pool, so at most pool_bytes of query data are ever in flight;
-//   * as soon as one of `streams` stream slots is free, the waiting requests
-//     (in arrival order, up to max_batch_pairs and what the ring holds) are
-//     packed into that slot's pinned staging, copied to the device, answered
-//     by one query launch (k_query, one warp per pair) and copied back, all on
-//     the slot's stream; requests that arrive while earlier batches run on the
-//     GPU join the next batch, and batches on different slots overlap;
-//   * completion is detected with CUDA events, in launch order; results go to
-//     each request's output buffer and its latency (submit to completion on
-//     the host's steady clock) is recorded.
+// Memory. The server owns one ring of P pair slots, mirrored in pinned host
+// memory and in device memory: pairs (s, t) as 8 bytes each, results as 1
+// byte each, so the device holds 9 P bytes (pool_bytes). A request of q pairs
+// is ADMITTED when q contiguous slots are free: pll_server_submit blocks until
+// then, so at most P pairs are ever queued or in flight. The client's own
+// thread copies its pairs into its slots (checking every id on the way); the
+// slots stay held until the request's results are back.
+//
+// Continuous batching. One dispatcher thread takes, whenever one of `streams`
+// stream slots is free, the longest run of staged requests that are waiting
+// (arrival order, contiguous in the ring, at most max_batch_pairs pairs) and
+// launches it as one unit on that slot's stream: one copy of the run's pair
+// slots to the device, one query launch (k_query, a warp per pair, reading the
+// interleaved pairs in place), one copy of the run's results back, one event.
+// Requests that arrive while earlier runs are on the GPU form the next run,
+// and runs on different stream slots overlap on the device. Runs retire in
+// launch order: their results go to the requests' buffers, each request's
+// latency (submit to results delivered, host steady clock) is recorded, and
+// their slots return to the ring.
+//
 // A result does not depend on what it was batched with: each pair is answered
 // by its own warp from the immutable index.
 #include <algorithm>
@@ -27,6 +32,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -40,33 +46,30 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Request {
-    uint64_t ticket = 0;
-    const uint32_t *src = nullptr, *dst = nullptr;
-    uint64_t q = 0;
+    uint64_t ticket = 0;      // 0: a rejected request that still holds its slots
+    uint64_t off = 0, q = 0;  // its ring slots [off, off + q)
     uint8_t *out = nullptr;
     Clock::time_point t_submit;
     double latency_us = 0;
-    bool done = false;
+    bool staged = false, done = false;
     int status = PLL_OK;
 };
 
-struct Batch {
-    std::vector<Request *> reqs;
-    uint64_t pairs = 0;
-    uint64_t ring_off = 0, ring_bytes = 0;
+struct Run {
+    std::vector<Request *> reqs;  // consecutive in the ring
+    uint64_t off = 0, pairs = 0;
     int slot = -1;
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    uint32_t *h_src = nullptr, *h_dst = nullptr;  // pinned staging
-    uint8_t *h_out = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
     bool busy = false;
 };
 
-uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
-uint64_t batch_bytes(uint64_t q) { return 2 * align256(4 * q) + align256(q); }
+double us_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
 
 }  // namespace
 
@@ -74,13 +77,21 @@ struct pll_server {
     const pll_index *ix = nullptr;
     int device = 0;
     pll_server_opts opts{};
-    unsigned char *pool = nullptr;  // device ring of opts.pool_bytes
+    uint64_t P = 0;                   // ring slots (pairs)
+    uint64_t max_request = 0;         // largest request accepted
+    uint32_t *d_pairs = nullptr;      // device [P][2]
+    uint8_t *d_out = nullptr;         // device [P]
+    uint32_t *h_pairs = nullptr;      // pinned [P][2]
+    uint8_t *h_out = nullptr;         // pinned [P]
     std::vector<Slot> slots;
-    std::deque<Batch> inflight;     // dispatcher thread only; launch order == ring order
-    uint64_t inflight_bytes = 0;
-    std::mutex mu;                  // guards everything below
-    std::condition_variable cv_submit, cv_done;
-    std::deque<Request *> pending;
+    std::deque<Run> inflight;         // dispatcher thread only, launch order
+    double device_us = 0;             // dispatcher thread only
+    std::mutex mu;                    // guards everything below
+    std::condition_variable cv_work;  // dispatcher: a request was staged, or stop
+    std::condition_variable cv_done;  // clients: a request completed
+    std::condition_variable cv_space; // clients: ring slots were freed
+    std::deque<Request *> live;       // hold ring slots, ring order
+    size_t nlaunched = 0;             // live[0, nlaunched) belong to launched runs
     std::unordered_map<uint64_t, Request *> table;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -91,125 +102,135 @@ struct pll_server {
 
 namespace {
 
-// First-fit allocation in a FIFO ring over the device pool. Batches hold
-// [off, off + bytes) until they retire, oldest first, so the live blocks are
-// the in-flight batches in order: one run [front.off, back end), or two once
-// the ring has wrapped (back.off < front.off).
-bool ring_alloc(const std::deque<Batch> &live, uint64_t cap, uint64_t bytes, uint64_t *off) {
-    if (bytes > cap) return false;
+// First-fit allocation in the FIFO ring. The live requests hold, in order,
+// one run of slots [front.off, back end), or two once the ring has wrapped
+// (back.off < front.off); the slots skipped at the end when a request wraps
+// to 0 are free again once the requests before them retire.
+bool ring_alloc(const std::deque<Request *> &live, uint64_t cap, uint64_t q, uint64_t *off) {
+    if (q > cap) return false;
     if (live.empty()) { *off = 0; return true; }
-    const uint64_t first = live.front().ring_off;
-    const uint64_t end = live.back().ring_off + live.back().ring_bytes;
-    if (live.back().ring_off >= first) {  // not wrapped: free [end, cap) and [0, first)
-        if (cap - end >= bytes) { *off = end; return true; }
-        if (first >= bytes) { *off = 0; return true; }
+    const uint64_t first = live.front()->off;
+    const uint64_t end = live.back()->off + live.back()->q;
+    if (live.back()->off >= first) {  // not wrapped: free [end, cap) and [0, first)
+        if (cap - end >= q) { *off = end; return true; }
+        if (first >= q) { *off = 0; return true; }
         return false;
     }
-    if (first - end >= bytes) { *off = end; return true; }  // wrapped: free [end, first)
+    if (first - end >= q) { *off = end; return true; }  // wrapped: free [end, first)
     return false;
 }
 
-int launch_batch(pll_server *sv, const Batch &b) {
-    Slot &sl = sv->slots[b.slot];
-    uint64_t p = 0;
-    for (const Request *r : b.reqs) {
-        std::memcpy(sl.h_src + p, r->src, r->q * 4);
-        std::memcpy(sl.h_dst + p, r->dst, r->q * 4);
-        p += r->q;
-    }
-    unsigned char *base = sv->pool + b.ring_off;
-    uint32_t *d_src = reinterpret_cast<uint32_t *>(base);
-    uint32_t *d_dst = reinterpret_cast<uint32_t *>(base + align256(4 * b.pairs));
-    uint8_t *d_out = base + 2 * align256(4 * b.pairs);
-    PLL_TRY(cudaMemcpyAsync(d_src, sl.h_src, b.pairs * 4, cudaMemcpyHostToDevice, sl.stream));
-    PLL_TRY(cudaMemcpyAsync(d_dst, sl.h_dst, b.pairs * 4, cudaMemcpyHostToDevice, sl.stream));
-    PLL_CHECK(pll::query_launch(sv->ix, d_src, d_dst, b.pairs, d_out, sl.stream));
-    PLL_TRY(cudaMemcpyAsync(sl.h_out, d_out, b.pairs, cudaMemcpyDeviceToHost, sl.stream));
+uint64_t ring_used(const std::deque<Request *> &live, uint64_t cap) {
+    if (live.empty()) return 0;
+    const uint64_t first = live.front()->off;
+    const uint64_t end = live.back()->off + live.back()->q;
+    return live.back()->off >= first ? end - first : cap - first + end;
+}
+
+int launch_run(pll_server *sv, const Run &r) {
+    const Slot &sl = sv->slots[r.slot];
+    uint32_t *dp = sv->d_pairs + 2 * r.off;
+    PLL_TRY(cudaEventRecord(sl.start, sl.stream));
+    PLL_TRY(cudaMemcpyAsync(dp, sv->h_pairs + 2 * r.off, r.pairs * 8, cudaMemcpyHostToDevice,
+                            sl.stream));
+    PLL_CHECK(pll::query_launch_strided(sv->ix, dp, dp + 1, 2, r.pairs, sv->d_out + r.off, sl.stream));
+    PLL_TRY(cudaMemcpyAsync(sv->h_out + r.off, sv->d_out + r.off, r.pairs, cudaMemcpyDeviceToHost,
+                            sl.stream));
     PLL_TRY(cudaEventRecord(sl.done, sl.stream));
     return PLL_OK;
 }
 
-void finish_batch(pll_server *sv, const Batch &b, int status) {
-    Slot &sl = sv->slots[b.slot];
+// Deliver a run's results and return its slots to the ring.
+void retire_run(pll_server *sv, const Run &r, int status) {
+    const Clock::time_point t0 = Clock::now();
+    if (status == PLL_OK)
+        for (const Request *q : r.reqs)  // the caller's buffer is ours until done is set
+            if (q->ticket) std::memcpy(q->out, sv->h_out + q->off, q->q);
     const Clock::time_point now = Clock::now();
-    std::lock_guard<std::mutex> lock(sv->mu);
-    uint64_t p = 0;
-    for (Request *r : b.reqs) {
-        if (status == PLL_OK) std::memcpy(r->out, sl.h_out + p, r->q);
-        p += r->q;
-        r->latency_us = std::chrono::duration<double, std::micro>(now - r->t_submit).count();
-        r->status = status;
-        r->done = true;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        for (Request *q : r.reqs) {
+            if (q->ticket == 0) { delete q; continue; }
+            q->latency_us = us_between(q->t_submit, now);
+            q->status = status;
+            q->done = true;
+        }
+        for (size_t i = 0; i < r.reqs.size(); ++i) sv->live.pop_front();
+        sv->nlaunched -= r.reqs.size();
+        sv->slots[r.slot].busy = false;
+        sv->st.unpack_us += us_between(t0, now);
+        sv->st.device_us = sv->device_us;
     }
-    sl.busy = false;
     sv->cv_done.notify_all();
+    sv->cv_space.notify_all();
 }
 
 void worker_loop(pll_server *sv) {
     cudaSetDevice(sv->device);
-    const uint64_t cap = sv->opts.pool_bytes;
+    // after work the dispatcher polls for SPIN_US before it sleeps on the
+    // condition variable: a thread woken from sleep adds tens of microseconds
+    constexpr int SPIN_US = 1000;
+    Clock::time_point last_work = Clock::now();
     for (;;) {
-        // 1. retire finished batches, oldest first
+        // 1. retire finished runs, oldest first
         while (!sv->inflight.empty()) {
-            const Batch &b = sv->inflight.front();
-            const cudaError_t e = cudaEventQuery(sv->slots[b.slot].done);
+            const Run &r = sv->inflight.front();
+            const Slot &sl = sv->slots[r.slot];
+            const cudaError_t e = cudaEventQuery(sl.done);
             if (e == cudaErrorNotReady) break;
+            float ms = 0;
+            if (e == cudaSuccess && cudaEventElapsedTime(&ms, sl.start, sl.done) == cudaSuccess)
+                sv->device_us += 1e3 * ms;
             if (e != cudaSuccess) sv->fatal = PLL_E_CUDA;
-            finish_batch(sv, b, e == cudaSuccess ? PLL_OK : PLL_E_CUDA);
-            sv->inflight_bytes -= b.ring_bytes;
+            retire_run(sv, r, e == cudaSuccess ? PLL_OK : PLL_E_CUDA);
             sv->inflight.pop_front();
+            last_work = Clock::now();
         }
-        // 2. with a free stream slot, admit waiting requests into one batch
+        // 2. with a free stream slot, launch the staged requests as one run
         int slot = -1;
         for (size_t i = 0; i < sv->slots.size(); ++i)
             if (!sv->slots[i].busy) { slot = (int)i; break; }
-        Batch b;
+        Run run;
         bool quit = false;
         {
             std::unique_lock<std::mutex> lock(sv->mu);
-            if (sv->pending.empty() && sv->inflight.empty()) {
-                if (sv->stop) quit = true;
-                else sv->cv_submit.wait_for(lock, std::chrono::milliseconds(2),
-                                            [&] { return sv->stop || !sv->pending.empty(); });
+            auto ready = [sv] {
+                return sv->nlaunched < sv->live.size() && sv->live[sv->nlaunched]->staged;
+            };
+            if (!ready() && sv->inflight.empty()) {
+                if (sv->stop && sv->live.empty()) quit = true;
+                else if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US))
+                    sv->cv_work.wait_for(lock, std::chrono::milliseconds(2),
+                                         [&] { return sv->stop || ready(); });
             }
-            if (!quit && slot >= 0 && !sv->pending.empty()) {
-                uint64_t pairs = 0;
-                size_t take = 0;
-                for (const Request *r : sv->pending) {
-                    if (take > 0 && pairs + r->q > sv->opts.max_batch_pairs) break;
-                    pairs += r->q;
-                    ++take;
+            if (!quit && slot >= 0 && ready()) {
+                run.off = sv->live[sv->nlaunched]->off;
+                for (size_t i = sv->nlaunched; i < sv->live.size(); ++i) {
+                    Request *q = sv->live[i];
+                    if (!q->staged || q->off != run.off + run.pairs) break;  // not staged, or wrapped
+                    if (!run.reqs.empty() && run.pairs + q->q > sv->opts.max_batch_pairs) break;
+                    run.reqs.push_back(q);
+                    run.pairs += q->q;
                 }
-                uint64_t off = 0;
-                while (take > 0 && !ring_alloc(sv->inflight, cap, batch_bytes(pairs), &off))
-                    pairs -= sv->pending[--take]->q;  // shrink until the block fits
-                if (take > 0) {
-                    b.reqs.assign(sv->pending.begin(), sv->pending.begin() + take);
-                    sv->pending.erase(sv->pending.begin(), sv->pending.begin() + take);
-                    b.pairs = pairs;
-                    b.ring_off = off;
-                    b.ring_bytes = batch_bytes(pairs);
-                    b.slot = slot;
-                    sv->slots[slot].busy = true;
-                    sv->st.batches++;
-                    sv->st.max_batch_pairs = std::max(sv->st.max_batch_pairs, pairs);
-                    sv->st.max_inflight_bytes =
-                        std::max(sv->st.max_inflight_bytes, sv->inflight_bytes + b.ring_bytes);
-                }
+                sv->nlaunched += run.reqs.size();
+                run.slot = slot;
+                sv->slots[slot].busy = true;
+                sv->st.batches++;
+                sv->st.max_batch_pairs = std::max(sv->st.max_batch_pairs, run.pairs);
             }
         }
         if (quit) return;
-        if (b.slot >= 0) {
-            const int s = launch_batch(sv, b);
-            if (s != PLL_OK) {  // nothing of the batch is in flight once the stream drains
-                cudaStreamSynchronize(sv->slots[b.slot].stream);
+        if (run.slot >= 0) {
+            const int s = launch_run(sv, run);
+            if (s != PLL_OK) {  // nothing of the run is in flight once the stream drains
+                cudaStreamSynchronize(sv->slots[run.slot].stream);
                 sv->fatal = s;
-                finish_batch(sv, b, s);
+                retire_run(sv, run, s);
                 continue;
             }
-            sv->inflight_bytes += b.ring_bytes;
-            sv->inflight.push_back(std::move(b));
-        } else if (!sv->inflight.empty()) {
+            sv->inflight.push_back(std::move(run));
+            last_work = Clock::now();
+        } else {
             std::this_thread::yield();
         }
     }
@@ -218,20 +239,17 @@ void worker_loop(pll_server *sv) {
 void destroy(pll_server *sv) {
     for (Slot &sl : sv->slots) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.start) cudaEventDestroy(sl.start);
         if (sl.done) cudaEventDestroy(sl.done);
-        if (sl.h_src) cudaFreeHost(sl.h_src);
-        if (sl.h_dst) cudaFreeHost(sl.h_dst);
-        if (sl.h_out) cudaFreeHost(sl.h_out);
     }
-    if (sv->pool) cudaFree(sv->pool);
-    for (auto &kv : sv->table) delete kv.second;
+    if (sv->d_pairs) cudaFree(sv->d_pairs);
+    if (sv->h_pairs) cudaFreeHost(sv->h_pairs);
+    // a request is in `live` until it completes, and in `table` from staging
+    // until it is waited for: completed ones are only in the table
+    for (auto &kv : sv->table)
+        if (kv.second->done) delete kv.second;
+    for (Request *r : sv->live) delete r;
     delete sv;
-}
-
-int check_ids(const uint32_t *v, uint64_t q, uint32_t n) {
-    for (uint64_t i = 0; i < q; ++i)
-        if (v[i] >= n) return PLL_E_INVAL;
-    return PLL_OK;
 }
 
 }  // namespace
@@ -247,28 +265,28 @@ PLL_API int pll_server_start(const pll_index *idx, const pll_server_opts *opts, 
     if (o.pool_bytes == 0) o.pool_bytes = 256ull << 20;
     if (o.max_batch_pairs == 0) o.max_batch_pairs = 1u << 20;
     if (o.streams == 0) o.streams = 4;
-    if (o.streams > 64 || o.pool_bytes < batch_bytes(1)) return PLL_E_INVAL;
-    // a batch never holds more pairs than the pool has room for
-    uint64_t fit = o.pool_bytes / 9;
-    while (fit > 0 && batch_bytes(fit) > o.pool_bytes) --fit;
-    o.max_batch_pairs = std::min<uint64_t>(o.max_batch_pairs, fit);
+    const uint64_t P = o.pool_bytes / 9;
+    if (o.streams > 64 || P == 0) return PLL_E_INVAL;
     pll_server *sv = new (std::nothrow) pll_server();
     if (!sv) return PLL_E_NOMEM;
     sv->ix = idx;
     sv->opts = o;
     sv->device = idx->device;
-    sv->st.pool_bytes = o.pool_bytes;
-    sv->st.max_request_pairs = o.max_batch_pairs;
+    sv->P = P;
+    sv->max_request = std::min<uint64_t>(o.max_batch_pairs, P);
+    sv->st.pool_bytes = 9 * P;
+    sv->st.max_request_pairs = sv->max_request;
     cudaError_t e = cudaSetDevice(sv->device);
-    if (e == cudaSuccess) e = cudaMalloc(&sv->pool, o.pool_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_pairs, 9 * P);
+    if (e == cudaSuccess) e = cudaMallocHost(&sv->h_pairs, 9 * P);
     if (e == cudaSuccess) {
+        sv->d_out = reinterpret_cast<uint8_t *>(sv->d_pairs + 2 * P);
+        sv->h_out = reinterpret_cast<uint8_t *>(sv->h_pairs + 2 * P);
         sv->slots.resize(o.streams);
         for (Slot &sl : sv->slots) {
             if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaMallocHost(&sl.h_src, o.max_batch_pairs * 4);
-            if (e == cudaSuccess) e = cudaMallocHost(&sl.h_dst, o.max_batch_pairs * 4);
-            if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, o.max_batch_pairs);
+            if (e == cudaSuccess) e = cudaEventCreate(&sl.start);
+            if (e == cudaSuccess) e = cudaEventCreate(&sl.done);
         }
     }
     if (e != cudaSuccess) {
@@ -290,27 +308,46 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
                               uint8_t *out, uint64_t *ticket) {
     if (!sv || !ticket || q == 0 || !src || !dst || !out) return PLL_E_INVAL;
     *ticket = 0;
-    if (q > sv->opts.max_batch_pairs) return PLL_E_RANGE;
-    PLL_CHECK(check_ids(src, q, sv->ix->n));
-    PLL_CHECK(check_ids(dst, q, sv->ix->n));
+    if (q > sv->max_request) return PLL_E_RANGE;
     Request *r = new (std::nothrow) Request();
     if (!r) return PLL_E_NOMEM;
-    r->src = src;
-    r->dst = dst;
     r->q = q;
     r->out = out;
+    r->t_submit = Clock::now();
+    {
+        std::unique_lock<std::mutex> lock(sv->mu);
+        uint64_t off = 0;
+        sv->cv_space.wait(lock, [&] { return sv->stop || ring_alloc(sv->live, sv->P, q, &off); });
+        if (sv->stop) { delete r; return PLL_E_INVAL; }
+        r->off = off;
+        r->ticket = sv->next_ticket++;
+        sv->live.push_back(r);
+        sv->st.max_inflight_bytes = std::max(sv->st.max_inflight_bytes, 9 * ring_used(sv->live, sv->P));
+    }
+    // stage the pairs into the request's own slots, checking the ids on the way
+    const Clock::time_point t0 = Clock::now();
+    const uint32_t n = sv->ix->n;
+    uint32_t *h = sv->h_pairs + 2 * r->off;
+    uint32_t bad = 0;
+    for (uint64_t i = 0; i < q; ++i) {
+        const uint32_t a = src[i], b = dst[i];
+        bad |= (uint32_t)(a >= n) | (uint32_t)(b >= n);
+        h[2 * i] = a < n ? a : 0;
+        h[2 * i + 1] = b < n ? b : 0;
+    }
+    const uint64_t tk = r->ticket;
     {
         std::lock_guard<std::mutex> lock(sv->mu);
-        if (sv->stop) { delete r; return PLL_E_INVAL; }
-        r->ticket = sv->next_ticket++;
-        r->t_submit = Clock::now();
-        sv->table[r->ticket] = r;
-        sv->pending.push_back(r);
+        if (bad) r->ticket = 0;  // keeps its slots until its run retires, answers nobody
+        else sv->table[tk] = r;
+        r->staged = true;
         sv->st.requests++;
         sv->st.pairs += q;
+        sv->st.pack_us += us_between(t0, Clock::now());
     }
-    sv->cv_submit.notify_one();
-    *ticket = r->ticket;
+    sv->cv_work.notify_one();
+    if (bad) return PLL_E_INVAL;
+    *ticket = tk;
     return PLL_OK;
 }
 
@@ -333,46 +370,57 @@ PLL_API int pll_server_wait(pll_server *sv, uint64_t ticket, int64_t timeout_us,
 
 PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_t *dst,
                               const uint64_t *req_off, const double *arrival_us, uint64_t count,
-                              uint8_t *out, double *latency_us, double *elapsed_us) {
-    if (!sv || !req_off || (count > 0 && (!src || !dst || !out || !arrival_us || !latency_us)))
+                              uint32_t threads, uint8_t *out, double *latency_us,
+                              double *elapsed_us) {
+    if (!sv || !req_off || threads > 64 ||
+        (count > 0 && (!src || !dst || !out || !arrival_us || !latency_us)))
         return PLL_E_INVAL;
     for (uint64_t i = 0; i < count; ++i)
         if (req_off[i + 1] <= req_off[i] || (i > 0 && arrival_us[i] < arrival_us[i - 1]))
             return PLL_E_INVAL;
+    if (threads == 0) threads = 1;
+    // client thread k submits requests k, k + threads, ... at their arrival
+    // times; one collector waits for them in order
     std::vector<uint64_t> tickets(count, 0);
-    std::atomic<uint64_t> submitted{0};
+    std::unique_ptr<std::atomic<uint8_t>[]> posted(new (std::nothrow) std::atomic<uint8_t>[count ? count : 1]);
+    if (!posted) return PLL_E_NOMEM;
+    for (uint64_t i = 0; i < count; ++i) posted[i].store(0, std::memory_order_relaxed);
     std::atomic<int> first_err{PLL_OK};
     auto note = [&first_err](int s) {
         int ok = PLL_OK;
         if (s != PLL_OK) first_err.compare_exchange_strong(ok, s);
     };
     for (uint64_t i = 0; i < count; ++i) latency_us[i] = -1;
-    std::thread collector;
+    const Clock::time_point t0 = Clock::now();
+    auto client = [&](uint32_t k) {
+        for (uint64_t i = k; i < count; i += threads) {
+            const Clock::time_point due = t0 + std::chrono::duration_cast<Clock::duration>(
+                                                   std::chrono::duration<double, std::micro>(arrival_us[i]));
+            for (Clock::time_point now = Clock::now(); now < due; now = Clock::now())
+                if (due - now > std::chrono::microseconds(200))
+                    std::this_thread::sleep_for(due - now - std::chrono::microseconds(100));
+            if (first_err.load() == PLL_OK) {
+                const uint64_t a = req_off[i], q = req_off[i + 1] - a;
+                note(pll_server_submit(sv, src + a, dst + a, q, out + a, &tickets[i]));
+            }
+            posted[i].store(1, std::memory_order_release);
+        }
+    };
+    std::vector<std::thread> pool;
     try {
-        collector = std::thread([&] {
+        for (uint32_t k = 1; k < threads; ++k) pool.emplace_back(client, k);
+        pool.emplace_back([&] {
             for (uint64_t i = 0; i < count; ++i) {
-                while (submitted.load(std::memory_order_acquire) <= i) std::this_thread::yield();
+                while (!posted[i].load(std::memory_order_acquire)) std::this_thread::yield();
                 if (tickets[i] != 0) note(pll_server_wait(sv, tickets[i], -1, &latency_us[i]));
             }
         });
-    } catch (...) {
-        return PLL_E_NOMEM;
+    } catch (...) {  // the collector starts last: without it nothing waits on `posted`
+        note(PLL_E_NOMEM);
     }
-    const Clock::time_point t0 = Clock::now();
-    for (uint64_t i = 0; i < count; ++i) {
-        const Clock::time_point due = t0 + std::chrono::duration_cast<Clock::duration>(
-                                               std::chrono::duration<double, std::micro>(arrival_us[i]));
-        for (Clock::time_point now = Clock::now(); now < due; now = Clock::now())
-            if (due - now > std::chrono::microseconds(200))
-                std::this_thread::sleep_for(due - now - std::chrono::microseconds(100));
-        if (first_err.load() == PLL_OK) {
-            const uint64_t a = req_off[i], q = req_off[i + 1] - a;
-            note(pll_server_submit(sv, src + a, dst + a, q, out + a, &tickets[i]));
-        }
-        submitted.store(i + 1, std::memory_order_release);
-    }
-    collector.join();
-    if (elapsed_us) *elapsed_us = std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
+    client(0);
+    for (std::thread &th : pool) th.join();
+    if (elapsed_us) *elapsed_us = us_between(t0, Clock::now());
     return first_err.load();
 }
 
@@ -389,7 +437,8 @@ PLL_API int pll_server_stop(pll_server *sv) {
         std::lock_guard<std::mutex> lock(sv->mu);
         sv->stop = true;
     }
-    sv->cv_submit.notify_all();
+    sv->cv_work.notify_all();
+    sv->cv_space.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     const int s = sv->fatal;
     destroy(sv);

@@ -58,7 +58,8 @@ class ServerOpts(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("requests", C.c_uint64), ("pairs", C.c_uint64), ("batches", C.c_uint64),
                 ("max_batch_pairs", C.c_uint64), ("max_inflight_bytes", C.c_uint64),
-                ("pool_bytes", C.c_uint64), ("max_request_pairs", C.c_uint64)]
+                ("pool_bytes", C.c_uint64), ("max_request_pairs", C.c_uint64),
+                ("pack_us", C.c_double), ("unpack_us", C.c_double), ("device_us", C.c_double)]
 
 
 class PLLError(RuntimeError):
@@ -128,7 +129,7 @@ def load(build_if_missing: bool = True):
     lib.pll_server_wait.restype = i32
     lib.pll_server_wait.argtypes = [vp, u64, C.c_int64, dp]
     lib.pll_server_replay.restype = i32
-    lib.pll_server_replay.argtypes = [vp, vp, vp, vp, vp, u64, vp, vp, dp]
+    lib.pll_server_replay.argtypes = [vp, vp, vp, vp, vp, u64, u32, vp, vp, dp]
     lib.pll_server_get_stats.restype = i32
     lib.pll_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
     lib.pll_server_stop.restype = i32
@@ -373,7 +374,7 @@ class Server:
         tk = C.c_uint64(0)
         _check(self._lib.pll_server_submit(self._h, sp, dp, len(s), out.ctypes.data,
                                            C.byref(tk)), "pll_server_submit")
-        self._live[tk.value] = (s, d, out)
+        self._live[tk.value] = (s, out)  # the server writes `out` until waited for
         return tk.value
 
     def wait(self, ticket: int, timeout_us: int = -1):
@@ -382,12 +383,13 @@ class Server:
         code = self._lib.pll_server_wait(self._h, ticket, timeout_us, C.byref(lat))
         if code == PLL_E_TIMEOUT:
             raise TimeoutError(f"request {ticket} not done after {timeout_us} us")
-        s, _, out = self._live.pop(ticket)
+        s, out = self._live.pop(ticket)
         _check(code, "pll_server_wait")
         return out[: len(s)], float(lat.value)
 
-    def replay(self, src, dst, req_off, arrival_us):
-        """Open-loop replay; returns (out uint8[total], latency_us[count], elapsed_us)."""
+    def replay(self, src, dst, req_off, arrival_us, threads: int = 4):
+        """Open-loop replay by `threads` client threads; returns
+        (out uint8[total], latency_us[count], elapsed_us)."""
         s, sp = _hptr(src, np.uint32)
         d, dp = _hptr(dst, np.uint32)
         off, op = _hptr(req_off, np.uint64)
@@ -397,14 +399,15 @@ class Server:
         out = np.empty(max(len(s), 1), dtype=np.uint8)
         lat = np.empty(max(count, 1), dtype=np.float64)
         el = C.c_double(0)
-        _check(self._lib.pll_server_replay(self._h, sp, dp, op, ap, count, out.ctypes.data,
+        _check(self._lib.pll_server_replay(self._h, sp, dp, op, ap, count, threads, out.ctypes.data,
                                            lat.ctypes.data, C.byref(el)), "pll_server_replay")
         return out[: len(s)], lat[:count], float(el.value)
 
     def stats(self) -> dict:
         st = ServerStats()
         _check(self._lib.pll_server_get_stats(self._h, C.byref(st)), "pll_server_get_stats")
-        return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+        return {f: (round(getattr(st, f), 1) if t is C.c_double else int(getattr(st, f)))
+                for f, t in ServerStats._fields_}
 
     def stop(self):
         if getattr(self, "_h", None):

@@ -65,6 +65,9 @@ def check_batch(gl, t, sample_pairs=2000, oracle_graphs=None, **kw):
         ug = np.searchsorted(start, u, side="right") - 1
         got = gpu_query(ix, s, u)
         assert (got[og != ug] == 255).all()
+        # small launches take the several-warps-per-pair path
+        for q in (1, 9, 300):
+            assert np.array_equal(gpu_query(ix, s[:q], u[:q]), got[:q]), q
     return ix
 
 

@@ -165,3 +165,32 @@ def test_empty_and_tiny():
     for g in (graphs.complete(1), gg.from_edges(10, [], []), graphs.complete(2)):
         for t in (0, 1, 64):
             check_index(g, t)
+
+
+@pytest.mark.parametrize("t", [0, 64])
+def test_query_launch_sizes(t):
+    """Launches of every size class: a few pairs (8 warps per pair), up to
+    one, two and four pairs per resident block (8, 4, 2 warps per pair), and
+    large launches (one warp per pair); each also with a bad id, which must
+    answer 255 and be counted."""
+    import torch
+    from paper_1304_4661_gb300 import pll
+    g = gg.rmat(13, 16, seed=3)
+    ix, ref = check_index(g, t)
+    props = torch.cuda.get_device_properties(0)
+    res = props.multi_processor_count * 8  # resident 256-thread blocks, upper bound
+    sizes = sorted({1, 2, 7, 33, res // 2, res, res + 1, 2 * res - 1, 2 * res + 3, 4 * res - 5,
+                    4 * res + 7, 10 * res, 200_000})
+    for q in sizes:
+        s, u = gg.pairs(g.n, q, 100 + q)
+        expect = ref.query_batch(s, u)
+        assert np.array_equal(gpu_query(ix, s, u), expect), q
+        bad = s.copy()
+        bad[q // 2] = g.n
+        out = torch.empty(q, dtype=torch.uint8, device="cuda")
+        ix.query_async(dev_u32(bad), dev_u32(u), out)
+        assert ix.query_errors() == 1, q
+        got = out.cpu().numpy()
+        assert got[q // 2] == 255
+        keep = np.arange(q) != q // 2
+        assert np.array_equal(got[keep], expect[keep]), q

@@ -102,3 +102,31 @@ def test_rejections(served):
         assert d.tolist() == [0]
     with pytest.raises(pll.PLLError):
         pll.Server(ix, streams=65)
+
+
+def test_concurrent_clients(served):
+    """Several client threads submit and wait at once (the binding releases
+    the GIL inside each call); every answer still matches the oracle."""
+    import threading
+    g, ix, ref = served
+    s, t, off, _ = requests(g, 240, 16)
+    expect = ref.query_batch(s, t)
+    got = [None] * (len(off) - 1)
+    errors = []
+    with pll.Server(ix, pool_bytes=1 << 20, streams=3) as sv:
+        def client(k):
+            try:
+                for i in range(k, len(off) - 1, 4):
+                    a, b = off[i], off[i + 1]
+                    got[i] = sv.wait(sv.submit(s[a:b], t[a:b]))[0]
+            except Exception as e:  # surfaced below
+                errors.append(e)
+        th = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        st = sv.stats()
+    assert not errors, errors
+    assert np.array_equal(np.concatenate(got), expect)
+    assert st["requests"] == len(off) - 1
