@@ -78,6 +78,8 @@ def _load():
         lib.orc_counters.argtypes = [vp, vp]
         lib.orc_label_of.restype = i64
         lib.orc_label_of.argtypes = [u32, vp, vp, vp, vp, u32, vp, vp]
+        lib.orc_core_numbers.restype = i32
+        lib.orc_core_numbers.argtypes = [u32, vp, vp, vp]
         lib.orc_export_rank_inX.restype = None
         lib.orc_export_rank_inX.argtypes = [vp, vp, vp]
         _lib = lib
@@ -101,6 +103,17 @@ def degree_order(offsets, cols) -> np.ndarray:
     st = _load().orc_degree_order(n, off.ctypes.data, col.ctypes.data, out.ctypes.data)
     if st:
         raise OracleError(st, "degree_order")
+    return out[:n]
+
+
+def core_numbers(offsets, cols) -> np.ndarray:
+    """Core number of every vertex (bucket peeling, see oracle.c)."""
+    off, col = _u32(offsets), _u32(cols)
+    n = off.shape[0] - 1
+    out = np.empty(max(n, 1), dtype=np.uint32)
+    st = _load().orc_core_numbers(n, off.ctypes.data, col.ctypes.data, out.ctypes.data)
+    if st:
+        raise OracleError(st, "core_numbers")
     return out[:n]
 
 

@@ -30,6 +30,13 @@
  *                         pruning (Sec. 5.4). One BFS from u with a dynamic
  *                         program over shortest-path predecessors.
  *
+ *   orc_core_numbers   -- core number of every vertex (the largest k such that
+ *                         the vertex lies in a subgraph of minimum degree k),
+ *                         one of the vertex features of the learned order; the
+ *                         paper has no counterpart. Bucket peeling in the
+ *                         manner of Batagelj and Zaversnik (2003): repeatedly
+ *                         remove a vertex of least remaining degree.
+ *
  * Readings of the paper taken here (each one is listed in the design notes):
  *   - Alg. 1 appends (v_k, P[u]) to L(u) and expands N_G(u) (the printed
  *     algorithm has typos there); the prune test is "<=".
@@ -516,4 +523,56 @@ out:
 void orc_export_rank_inX(const orc_index *ix, uint32_t *rank, uint8_t *inX) {
     memcpy(rank, ix->rank, (size_t)ix->n * sizeof(uint32_t));
     memcpy(inX, ix->inX, ix->n);
+}
+
+/* Core numbers by bucket peeling: vertices are kept sorted by their current
+ * degree in `vert` (bucket d starts at bin[d]); removing the vertex of least
+ * degree lowers each neighbour of larger degree by one, moving it to the front
+ * of its bucket first so the array stays sorted. The degree a vertex has when
+ * it is removed is its core number. */
+int orc_core_numbers(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t *core) {
+    if (n == 0) return ORC_OK;
+    uint32_t md = 0;
+    uint32_t *deg = malloc(sizeof(uint32_t) * n), *pos = malloc(sizeof(uint32_t) * n);
+    uint32_t *vert = malloc(sizeof(uint32_t) * n);
+    for (uint32_t v = 0; v < n; ++v) {
+        deg[v] = off[v + 1] - off[v];
+        if (deg[v] > md) md = deg[v];
+    }
+    uint32_t *bin = calloc((size_t)md + 2, sizeof(uint32_t));
+    if (!deg || !pos || !vert || !bin) {
+        free(deg); free(pos); free(vert); free(bin);
+        return ORC_E_NOMEM;
+    }
+    for (uint32_t v = 0; v < n; ++v) bin[deg[v]]++;
+    uint32_t start = 0;
+    for (uint32_t d = 0; d <= md; ++d) {
+        uint32_t c = bin[d];
+        bin[d] = start;
+        start += c;
+    }
+    for (uint32_t v = 0; v < n; ++v) {
+        pos[v] = bin[deg[v]]++;
+        vert[pos[v]] = v;
+    }
+    for (uint32_t d = md; d > 0; --d) bin[d] = bin[d - 1];
+    bin[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t v = vert[i];
+        for (uint32_t e = off[v]; e < off[v + 1]; ++e) {
+            uint32_t u = col[e];
+            if (deg[u] > deg[v]) {
+                uint32_t du = deg[u], pu = pos[u], pw = bin[du], w = vert[pw];
+                if (u != w) {
+                    pos[u] = pw; vert[pu] = w;
+                    pos[w] = pu; vert[pw] = u;
+                }
+                bin[du]++;
+                deg[u]--;
+            }
+        }
+    }
+    memcpy(core, deg, sizeof(uint32_t) * n);
+    free(deg); free(pos); free(vert); free(bin);
+    return ORC_OK;
 }

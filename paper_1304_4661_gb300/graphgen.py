@@ -202,3 +202,18 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
     gaps = -np.log1p(-u) / rate_per_s * 1e6
     out = np.cumsum(gaps)
     return out - out[0] if count else out
+
+
+MLP_NPARAM = 4801  # 8 -> 64 -> 64 -> 1: W1 [64][8], b1 [64], W2 [64][64], b2 [64], w3 [64], b3
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Initial parameters of the vertex-scoring network, float32[4801] in the
+    layout W1 [64][8], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 [1]:
+    weights He-uniform, U(-a, a) with a = sqrt(6 / fan_in), from the seeded
+    uniform generator; biases zero."""
+    u = uniform(seed, MLP_NPARAM)
+    p = np.zeros(MLP_NPARAM)
+    for lo, hi, fan in ((0, 512, 8), (576, 4672, 64), (4736, 4800, 64)):
+        p[lo:hi] = (2 * u[lo:hi] - 1) * math.sqrt(6.0 / fan)
+    return p.astype(np.float32)
