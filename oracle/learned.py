@@ -95,10 +95,12 @@ def features(offsets, cols, t: int):
     X[:, 3:] = bp
     if n == 0:
         return X
+    # a column of equal values has std 0 exactly; test that directly, since
+    # the float64 mean of equal values need not equal them
+    ok = X.max(axis=0) > X.min(axis=0)
     mu = X.mean(axis=0)
     sd = np.sqrt(((X - mu) ** 2).mean(axis=0))
     Z = np.zeros_like(X)
-    ok = sd > 0
     Z[:, ok] = (X[:, ok] - mu[ok]) / sd[ok]
     return Z
 

@@ -113,6 +113,14 @@ def test_bit_parallel_s0_counts_equal_distance_members():
     assert bp[0].tolist() == [0, 0, 1, 0, 0]
 
 
+@pytest.mark.parametrize("g", [graphs.complete(6), graphs.cycle(9), gg.from_edges(4, [], [])],
+                         ids=lambda g: g.name)
+def test_features_of_vertex_transitive_graphs_are_zero(g):
+    """Every vertex looks the same, so every column is constant and
+    standardises to 0 exactly."""
+    assert not OL.features(g.offsets, g.cols, 4).any()
+
+
 def test_features_standardised():
     g = gg.rmat(11, 8, seed=5)
     Z = OL.features(g.offsets, g.cols, 16)
