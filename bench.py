@@ -580,6 +580,89 @@ def run_serve(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ learned order
+def run_learned(args, ws, rank, local):
+    """Learned order: features, targets and training on 200 R-MAT graphs
+    (scale uniform in 14-16, ef 16, seeds 1000-1199, t = 64, Degree-order
+    builds); evaluation on R-MAT-21 (seed 5), t = 64: index size and build
+    time with the network's order against the Degree order."""
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import learned as L
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+    t = 64
+    specs = gg.learned_training_specs(args.learned_graphs)
+    tg = [gg.rmat(sc, 16, seed=sd) for sc, sd in specs]
+    X, y, rows, hs = L.harvest(tg, t=t)
+    mlp, th = L.train(X, y, rows, epochs=args.learned_epochs, batch=16384, lr=2e-3)
+    del X, y, rows
+    g = gg.rmat(21, 16, seed=5)
+    d_off, d_col = L._dev(g.offsets), L._dev(g.cols)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def build(order=None):
+        ix = pll.Index.build(d_off, d_col, t=t, order=order)
+        e = ix.label_entries()
+        ix.close()
+        return e
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    order = mlp.order(d_off, d_col, t)
+    for _ in range(args.warmup):
+        build()
+        build(order)
+    clocks.start()
+    deg = [timed(build) for _ in range(args.steps)]
+    ords = [timed(lambda: mlp.order(d_off, d_col, t)) for _ in range(args.steps)]
+    lrn = [timed(lambda: build(ords[-1][1])) for _ in range(args.steps)]
+    clk = clocks.stop()
+    assert len({e for _, e in deg}) == 1 and len({e for _, e in lrn}) == 1
+    deg_ms = statistics.mean(x[0] for x in deg)
+    ord_ms = statistics.mean(x[0] for x in ords)
+    lrn_ms = statistics.mean(x[0] for x in lrn)
+    deg_e, lrn_e = deg[0][1], lrn[0][1]
+    out = {"metric": "C4 learned order, R-MAT-21 (t=64): build s with the network's order "
+                     "(order + build) vs Degree order",
+           "value": round((ord_ms + lrn_ms) / 1e3, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ord_ms + lrn_ms, 3), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8 labels, bf16/f32 network",
+           "data": "synthetic",
+           "config": {"workload": "train: 200 R-MAT (scale 14-16, ef 16, seeds 1000-1199), t=64; "
+                                  "eval: R-MAT-21 (ef 16, seed 5), t=64",
+                      "vertices": g.n, "arcs": g.nnz, "training_graphs": len(tg),
+                      "epochs": args.learned_epochs},
+           "degree": {"build_s": round(deg_ms / 1e3, 6), "label_entries": int(deg_e)},
+           "learned": {"order_s": round(ord_ms / 1e3, 6), "build_s": round(lrn_ms / 1e3, 6),
+                       "label_entries": int(lrn_e)},
+           "label_entries_ratio": round(lrn_e / deg_e, 4),
+           "build_time_ratio": round(lrn_ms / deg_ms, 4),
+           "harvest": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in hs.items()},
+           "training": {"steps": th["steps"], "seconds": round(th["seconds"], 3),
+                        "loss_first_last": [round(th["loss"][0][1], 5), round(th["loss"][-1][1], 5)]},
+           "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_baseline(args, scale=None):
     """The oracle as it stands (single thread) on a bounded sample: a full
@@ -643,7 +726,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve"], default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned"], default="rmat20")
     ap.add_argument("--root-batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--latency-samples", type=int, default=2000)
@@ -654,14 +737,17 @@ def main():
     ap.add_argument("--serve-plain", type=int, default=5000)
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-clients", type=int, default=4)
+    ap.add_argument("--learned-graphs", type=int, default=200)
+    ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload in ("batch256", "serve"):
+    if args.workload in ("batch256", "serve", "learned"):
         ws, rank, local = dist_setup()
-        (run_batch if args.workload == "batch256" else run_serve)(args, ws, rank, local)
+        {"batch256": run_batch, "serve": run_serve, "learned": run_learned}[args.workload](
+            args, ws, rank, local)
         return
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup() if args.impl == "ours" else (

@@ -348,6 +348,80 @@ PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_
 PLL_API int pll_server_get_stats(pll_server *sv, pll_server_stats *out);
 PLL_API int pll_server_stop(pll_server *sv);
 
+/*
+ * Learned vertex order. The labels are exact and minimal for any order
+ * (Thm 4.1, 4.2) but their size depends on it (Sec. 4.4, Table 4); besides
+ * the Degree order of Sec. 4.4.2 the library can order vertices by the score
+ * of a small network over per-vertex features. The paper has no such order.
+ *
+ * pll_features -- feat (device float[n][8], by caller id) receives, each
+ *   column standardised over the vertices ((x - mean) / population std, 0
+ *   where the std is 0): log(1 + deg), log(1 + sum of the neighbours'
+ *   degrees), log(1 + core number), and, from the bit-parallel labels of the
+ *   Degree order with t roots (t = 0: zeros) with d_i = min(d(r_i, v), 32):
+ *   mean d_i, min d_i, the share of i with d_i <= 2, mean |S^-1_{r_i}(v)| / 64
+ *   and mean |S^0_{r_i}(v)| / 64. core (device uint32[n]) and two_hop (device
+ *   uint64[n]) receive the raw core numbers and neighbour-degree sums; either
+ *   may be NULL. Same CSR rules and errors as pll_build. Synchronous.
+ *
+ * pll_hub_counts -- counts (device uint32[n], by caller id) = number of label
+ *   entries of idx whose hub is the vertex (vertices with none: 0, among them
+ *   every bit-parallel vertex); log1p_counts (device float[n] or NULL) =
+ *   log(1 + counts), the training target. Synchronous.
+ *
+ * pll_order_from_scores -- order (device uint32[n]) = vertices by descending
+ *   score (device float[n]), ties by ascending id; -0 equals +0, NaN last.
+ *   Synchronous.
+ *
+ * pll_mlp -- the scoring network 8 -> 64 -> 64 -> 1 with ReLU: 4801
+ *   parameters, float32 master copy and Adam moments on the device, a
+ *   bfloat16 copy used by every forward and backward pass (float32
+ *   arithmetic). Parameter layout: W1 [64][8], b1 [64], W2 [64][64], b2 [64],
+ *   w3 [64], b3 [1] (row j = weights into unit j).
+ *   pll_mlp_create      on the current device, for batches up to max_batch.
+ *   pll_mlp_set_params  host float[4801] -> master and bf16 copy; zeroes the
+ *                       Adam moments and step. Synchronous.
+ *   pll_mlp_get_params  master (host float[4801]) and/or bf16 copy (host
+ *                       uint16[4801] bit patterns). Synchronous.
+ *   pll_mlp_forward     y[i] = score of row i of x (device float[n][8]).
+ *   pll_mlp_grad        gradient of the mean squared error over the batch
+ *                       (row g = x[idx[g]] with target[idx[g]], or row g if
+ *                       idx is NULL; idx device uint32[batch]) with respect to
+ *                       the bf16 parameters, kept on the device with the loss;
+ *                       deterministic. PLL_E_RANGE if batch > max_batch.
+ *   pll_mlp_read_grad   gradient (host float[4801]) and/or loss (host float).
+ *                       Synchronous.
+ *   pll_mlp_adam        one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ *                       corrected) with the last gradient; refreshes the bf16
+ *                       copy.
+ *   pll_mlp_train_step  pll_mlp_grad then pll_mlp_adam.
+ *
+ * pll_learned_order -- pll_features, pll_mlp_forward and
+ *   pll_order_from_scores in one call; order (device uint32[n]) can be passed
+ *   to pll_build. Synchronous.
+ */
+typedef struct pll_mlp pll_mlp;
+
+PLL_API int pll_features(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t nnz,
+                         uint32_t t, void *stream, float *feat, uint32_t *core, uint64_t *two_hop);
+PLL_API int pll_hub_counts(const pll_index *idx, uint32_t *counts, float *log1p_counts,
+                           void *stream);
+PLL_API int pll_order_from_scores(const float *scores, uint32_t n, uint32_t *order, void *stream);
+PLL_API int pll_mlp_create(uint32_t max_batch, pll_mlp **out);
+PLL_API void pll_mlp_free(pll_mlp *mlp);
+PLL_API int pll_mlp_set_params(pll_mlp *mlp, const float *host_params, void *stream);
+PLL_API int pll_mlp_get_params(const pll_mlp *mlp, float *host_master, uint16_t *host_bf16);
+PLL_API int pll_mlp_forward(const pll_mlp *mlp, const float *x, uint64_t n, float *y, void *stream);
+PLL_API int pll_mlp_grad(pll_mlp *mlp, const float *x, const float *target, const uint32_t *idx,
+                         uint32_t batch, void *stream);
+PLL_API int pll_mlp_read_grad(const pll_mlp *mlp, float *host_grad, float *host_loss, void *stream);
+PLL_API int pll_mlp_adam(pll_mlp *mlp, float lr, void *stream);
+PLL_API int pll_mlp_train_step(pll_mlp *mlp, const float *x, const float *target,
+                               const uint32_t *idx, uint32_t batch, float lr, void *stream);
+PLL_API int pll_learned_order(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
+                              uint64_t nnz, uint32_t t, const pll_mlp *mlp, uint32_t *order,
+                              void *stream);
+
 /* Build statistics (sizes, per-phase times in milliseconds). */
 PLL_API int pll_get_stats(const pll_index *idx, pll_stats *out);
 

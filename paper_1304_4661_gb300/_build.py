@@ -29,6 +29,7 @@ CU_SOURCES = [
     "k_query.cu",
     "pll_noalloc.cu",
     "pll_serve.cu",
+    "k_learned.cu",
 ]
 
 

@@ -217,3 +217,13 @@ def mlp_init(seed: int) -> np.ndarray:
     for lo, hi, fan in ((0, 512, 8), (576, 4672, 64), (4736, 4800, 64)):
         p[lo:hi] = (2 * u[lo:hi] - 1) * math.sqrt(6.0 / fan)
     return p.astype(np.float32)
+
+
+def learned_training_specs(count: int = 200, seed: int = 11, scales=(14, 15, 16),
+                           first_seed: int = 1000):
+    """Training graphs of the learned order: R-MAT (ef 16, default a/b/c),
+    scale drawn uniformly from `scales`, graph seeds first_seed, first_seed + 1,
+    ... Returns a list of (scale, graph_seed)."""
+    u = uniform(seed, count)
+    k = len(scales)
+    return [(scales[min(k - 1, int(u[i] * k))], first_seed + i) for i in range(count)]

@@ -27,7 +27,11 @@ SYMBOLS = [
     "pll_bp_labels_noalloc", "pll_build_batch", "pll_autotune",
     "pll_server_start", "pll_server_submit", "pll_server_wait", "pll_server_replay",
     "pll_server_get_stats", "pll_server_stop",
+    "pll_features", "pll_hub_counts", "pll_order_from_scores", "pll_mlp_create", "pll_mlp_free",
+    "pll_mlp_set_params", "pll_mlp_get_params", "pll_mlp_forward", "pll_mlp_grad",
+    "pll_mlp_read_grad", "pll_mlp_adam", "pll_mlp_train_step", "pll_learned_order",
 ]
+MLP_NPARAM = 4801
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -134,6 +138,24 @@ def load(build_if_missing: bool = True):
     lib.pll_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
     lib.pll_server_stop.restype = i32
     lib.pll_server_stop.argtypes = [vp]
+    fp = C.c_float
+    for name, args in (("pll_features", [vp, vp, u32, u64, u32, vp, vp, vp, vp]),
+                       ("pll_hub_counts", [vp, vp, vp, vp]),
+                       ("pll_order_from_scores", [vp, u32, vp, vp]),
+                       ("pll_mlp_create", [u32, pp]),
+                       ("pll_mlp_set_params", [vp, vp, vp]),
+                       ("pll_mlp_get_params", [vp, vp, vp]),
+                       ("pll_mlp_forward", [vp, vp, u64, vp, vp]),
+                       ("pll_mlp_grad", [vp, vp, vp, vp, u32, vp]),
+                       ("pll_mlp_read_grad", [vp, vp, vp, vp]),
+                       ("pll_mlp_adam", [vp, fp, vp]),
+                       ("pll_mlp_train_step", [vp, vp, vp, vp, u32, fp, vp]),
+                       ("pll_learned_order", [vp, vp, u32, u64, u32, vp, vp, vp])):
+        f = getattr(lib, name)
+        f.restype = i32
+        f.argtypes = args
+    lib.pll_mlp_free.restype = None
+    lib.pll_mlp_free.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -311,6 +333,16 @@ class Index:
         _check(load().pll_label_entries(self._h, C.byref(c)), "pll_label_entries")
         return int(c.value)
 
+    def hub_counts(self, stream=None):
+        """pll_hub_counts: (counts int32 CUDA [n], log1p(counts) float32 CUDA [n])."""
+        import torch
+        n = max(self.n, 1)
+        c = torch.empty(n, dtype=torch.int32, device="cuda")
+        f = torch.empty(n, dtype=torch.float32, device="cuda")
+        _check(load().pll_hub_counts(self._h, _dptr(c), _dptr(f), _stream_handle(stream)),
+               "pll_hub_counts")
+        return c[: self.n], f[: self.n]
+
     def labels(self) -> Labels:
         tot = self.label_entries()
         off = np.empty(self.n + 1, dtype=np.uint64)
@@ -425,5 +457,116 @@ class Server:
     def __del__(self):
         try:
             self.stop()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ learned order
+def features(offsets, cols, t: int, out=None, raw: bool = False, stream=None):
+    """pll_features on CUDA tensors: float32 [n, 8] standardised features
+    (written into `out` if given); with raw=True also (core uint32, two_hop
+    uint64) as int tensors."""
+    import torch
+    n = int(offsets.shape[0]) - 1
+    nnz = int(cols.shape[0])
+    if out is None:
+        out = torch.empty((max(n, 0), 8), dtype=torch.float32, device=offsets.device)
+    core = two = None
+    if raw:
+        core = torch.empty(max(n, 1), dtype=torch.int32, device=offsets.device)
+        two = torch.empty(max(n, 1), dtype=torch.int64, device=offsets.device)
+    _check(load().pll_features(_dptr(offsets), _dptr(cols) if nnz else None, n, nnz, t,
+                               _stream_handle(stream), _dptr(out) if n else None,
+                               _dptr(core) if raw else None, _dptr(two) if raw else None),
+           "pll_features")
+    return (out, core[:n], two[:n]) if raw else out
+
+
+def order_from_scores(scores, stream=None):
+    """pll_order_from_scores: CUDA float32 scores -> CUDA int32 order."""
+    import torch
+    n = int(scores.shape[0])
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=scores.device)
+    _check(load().pll_order_from_scores(_dptr(scores) if n else None, n, _dptr(order),
+                                        _stream_handle(stream)), "pll_order_from_scores")
+    return order[:n]
+
+
+class MLP:
+    """pll_mlp: the vertex-scoring network (bf16 parameters, float32 master
+    copy and Adam state on the device)."""
+
+    def __init__(self, max_batch: int = 16384):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.pll_mlp_create(max_batch, C.byref(h)), "pll_mlp_create")
+        self._h = h.value
+        self.max_batch = max_batch
+
+    def set_params(self, params, stream=None):
+        p, pp = _hptr(params, np.float32)
+        assert p.shape == (MLP_NPARAM,)
+        _check(self._lib.pll_mlp_set_params(self._h, pp, _stream_handle(stream)), "pll_mlp_set_params")
+
+    def params(self):
+        """(float32 master [4801], bfloat16 bit patterns uint16 [4801])."""
+        m = np.empty(MLP_NPARAM, dtype=np.float32)
+        b = np.empty(MLP_NPARAM, dtype=np.uint16)
+        _check(self._lib.pll_mlp_get_params(self._h, m.ctypes.data, b.ctypes.data), "pll_mlp_get_params")
+        return m, b
+
+    def forward(self, x, out=None, stream=None):
+        import torch
+        n = int(x.shape[0])
+        if out is None:
+            out = torch.empty(max(n, 1), dtype=torch.float32, device=x.device)
+        _check(self._lib.pll_mlp_forward(self._h, _dptr(x) if n else None, n, _dptr(out),
+                                         _stream_handle(stream)), "pll_mlp_forward")
+        return out[:n]
+
+    def grad(self, x, target, idx=None, batch=None, stream=None):
+        """Gradient and loss of the mean squared error (host float32 [4801], float)."""
+        b = int(idx.shape[0]) if idx is not None else (batch or int(x.shape[0]))
+        sh = _stream_handle(stream)
+        _check(self._lib.pll_mlp_grad(self._h, _dptr(x), _dptr(target),
+                                      _dptr(idx) if idx is not None else None, b, sh), "pll_mlp_grad")
+        g = np.empty(MLP_NPARAM, dtype=np.float32)
+        loss = C.c_float(0)
+        _check(self._lib.pll_mlp_read_grad(self._h, g.ctypes.data, C.byref(loss), sh), "pll_mlp_read_grad")
+        return g, float(loss.value)
+
+    def adam(self, lr: float, stream=None):
+        _check(self._lib.pll_mlp_adam(self._h, lr, _stream_handle(stream)), "pll_mlp_adam")
+
+    def train_step(self, x, target, idx, lr: float, stream=None):
+        _check(self._lib.pll_mlp_train_step(self._h, _dptr(x), _dptr(target), _dptr(idx),
+                                            int(idx.shape[0]), lr, _stream_handle(stream)),
+               "pll_mlp_train_step")
+
+    def loss(self, stream=None) -> float:
+        v = C.c_float(0)
+        _check(self._lib.pll_mlp_read_grad(self._h, None, C.byref(v), _stream_handle(stream)),
+               "pll_mlp_read_grad")
+        return float(v.value)
+
+    def order(self, offsets, cols, t: int, stream=None):
+        """pll_learned_order: CUDA int32 order of the graph's vertices."""
+        import torch
+        n = int(offsets.shape[0]) - 1
+        nnz = int(cols.shape[0])
+        order = torch.empty(max(n, 1), dtype=torch.int32, device=offsets.device)
+        _check(self._lib.pll_learned_order(_dptr(offsets), _dptr(cols) if nnz else None, n, nnz, t,
+                                           self._h, _dptr(order), _stream_handle(stream)),
+               "pll_learned_order")
+        return order[:n]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pll_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
