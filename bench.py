@@ -46,8 +46,8 @@ WORKLOADS = {
 # for the kernel source with this hash (else traffic is reported as null).
 PROFILED = {
     # ncu, all 1150 launches of one R-MAT-20 build (profiles/k_batch_sweeps_rmat20.md)
-    "k_batch_expand": {"src_sha": "a6dd14a9fcfbabc5", "dram_bytes_per_launch": 153787301},
-    "k_batch_test": {"src_sha": "a6dd14a9fcfbabc5", "dram_bytes_per_launch": 129301271},
+    "k_batch_expand": {"src_sha": "3aa34b0d167958d9", "dram_bytes_per_launch": 153666052},
+    "k_batch_test": {"src_sha": "3aa34b0d167958d9", "dram_bytes_per_launch": 126646267},
 }
 
 

@@ -157,7 +157,9 @@ __global__ void k_ht_sizes(BatchArgs a, unsigned long long *sizes) {
 // Cheap part of the prune test, one thread: bit-parallel distances only.
 // Returns true if some d~_i <= level; else fills c1 / c2 with the roots whose
 // masks could still bring d~_i - reduction down to level.
+// wq: w's distance row, loaded by the caller (rows are tp bytes, tp <= 64)
 __device__ __forceinline__ bool bp_distance_test(const BatchArgs &a, const uint4 (&kr)[PLL_MAX_T / 16],
+                                                 const uint4 (&wq)[PLL_MAX_T / 16],
                                                  uint32_t k, uint32_t slot, uint32_t w,
                                                  uint32_t level, uint64_t &c1, uint64_t &c2) {
     c1 = c2 = 0;
@@ -169,7 +171,7 @@ __device__ __forceinline__ bool bp_distance_test(const BatchArgs &a, const uint4
 #pragma unroll
         for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
             if (c < (a.tp >> 4)) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(dw) + c);
+                const uint4 q = wq[c];
                 const uint4 r = kr[c];
                 const uint32_t wu[4] = {q.x, q.y, q.z, q.w}, wr[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -253,12 +255,21 @@ __global__ void __launch_bounds__(BLOCK) k_batch_expand(BatchArgs a) {
             if (x + lane < ee) {
                 w = a.rcol[x + lane];
                 uint32_t *word = &a.visited[(size_t)w * a.W + sw];
+                // w's distance row is requested together with the visited word
+                // (it is read-only), so a fresh claim does not wait for it after
+                // the atomic; rows of vertices already visited are fetched in vain
+                uint4 wq[PLL_MAX_T / 16];
+#pragma unroll
+                for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
+                    wq[c] = (c < (a.tp >> 4))
+                                ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
+                                : make_uint4(0, 0, 0, 0);
                 bool fresh = false;
                 if (!(*(volatile uint32_t *)word & sbit)) fresh = !(atomicOr(word, sbit) & sbit);
                 if (fresh) {
                     ++nclaim;
                     if (level + 1 >= INF8) atomicOr(&a.ctr->err, ERR_DEPTH);
-                    else keep = !bp_distance_test(a, kr, k, slot, w, level + 1, c1, c2) &&
+                    else keep = !bp_distance_test(a, kr, wq, k, slot, w, level + 1, c1, c2) &&
                                 !quick_masks(a, k, w, c1, c2);
                 }
             }
