@@ -663,6 +663,83 @@ def run_learned(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ paper variants
+def run_variants(args, ws, rank, local):
+    """Analogues of the paper's parameter studies on synthetic graphs: the
+    number of bit-parallel roots t (Fig. 6: index size, build and query time
+    against t) on R-MAT-20, and the vertex order (Table 4: Random vs Degree
+    label size, here with the learned order's sibling, random scores) on
+    R-MAT-14 and R-MAT-16 (Random order grows the index by orders of
+    magnitude, so the larger graphs are left out)."""
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    g = gg.rmat(20, 16, seed=1)
+    d_off, d_col = dev(g.offsets), dev(g.cols)
+    s, u = gg.pairs(g.n, 10_000_000, 3)
+    ds, du = dev(s), dev(u)
+    out = torch.empty(len(s), dtype=torch.uint8, device="cuda")
+    tsweep = []
+    for t in (0, 4, 16, 32, 64):
+        for _ in range(args.warmup):
+            pll.Index.build(d_off, d_col, t=t).close()
+        bt = []
+        for _ in range(args.steps):
+            ms, ix = timed(lambda: pll.Index.build(d_off, d_col, t=t))
+            bt.append(ms)
+            qms, _ = timed(lambda: ix.query_async(ds, du, out))
+            st = ix.stats()
+            ent = ix.label_entries()
+            ix.close()
+        tsweep.append({"t": t, "build_s": round(statistics.mean(bt) / 1e3, 4), "label_entries": ent,
+                       "avg_normal_label": round(ent / g.n, 2),
+                       "index_bytes": int(st["index_bytes"]),
+                       "queries_per_s": round(len(s) / (qms * 1e-3), 1)})
+    orders = []
+    for scale in (14, 16):
+        h = gg.rmat(scale, 16, seed=1)
+        o_off, o_col = dev(h.offsets), dev(h.cols)
+        rnd = pll.order_from_scores(torch.from_numpy(gg.uniform(21, h.n).astype(np.float32)).cuda())
+        row = {"graph": f"R-MAT-{scale}", "vertices": h.n}
+        for name, order in (("degree", None), ("random", rnd)):
+            ms, ix = timed(lambda: pll.Index.build(o_off, o_col, t=0, order=order))
+            row[name] = {"label_entries": ix.label_entries(), "build_s": round(ms / 1e3, 4)}
+            ix.close()
+        row["random_over_degree"] = round(row["random"]["label_entries"] / row["degree"]["label_entries"], 2)
+        orders.append(row)
+    outj = {"metric": "Paper variants: t sweep on R-MAT-20 (Fig. 6 analogue) and Random vs Degree "
+                      "order without bit-parallel labels (Table 4 analogue)",
+            "value": tsweep[-1]["build_s"], "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tsweep[-1]["build_s"] * 1e3, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": "R-MAT-20 (seed 1), 10M pairs (seed 3), t in {0,4,16,32,64}; "
+                                   "R-MAT-14/16 (seed 1), t = 0, Degree vs Random (scores seed 21)"},
+            "t_sweep": tsweep, "orders": orders}
+    if rank == 0:
+        print(json.dumps(outj), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_baseline(args, scale=None):
     """The oracle as it stands (single thread) on a bounded sample: a full
@@ -726,7 +803,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned"], default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned", "variants"], default="rmat20")
     ap.add_argument("--root-batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--latency-samples", type=int, default=2000)
@@ -744,10 +821,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload in ("batch256", "serve", "learned"):
+    if args.workload in ("batch256", "serve", "learned", "variants"):
         ws, rank, local = dist_setup()
-        {"batch256": run_batch, "serve": run_serve, "learned": run_learned}[args.workload](
-            args, ws, rank, local)
+        {"batch256": run_batch, "serve": run_serve, "learned": run_learned,
+         "variants": run_variants}[args.workload](args, ws, rank, local)
         return
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup() if args.impl == "ours" else (
