@@ -45,9 +45,10 @@ WORKLOADS = {
 # DRAM bytes per launch of the pruned-BFS kernel measured by ncu, valid only
 # for the kernel source with this hash (else traffic is reported as null).
 PROFILED = {
-    # ncu, all 1150 launches of one R-MAT-20 build (profiles/k_batch_sweeps_rmat20.md)
-    "k_batch_expand": {"src_sha": "3aa34b0d167958d9", "dram_bytes_per_launch": 153666052},
-    "k_batch_test": {"src_sha": "3aa34b0d167958d9", "dram_bytes_per_launch": 126646267},
+    # ncu, all 336 + 336 sweep launches of one R-MAT-20 build at the default
+    # root batch (profiles/k_batch_sweeps_rmat20.md); valid for that launch count
+    "k_batch_expand": {"src_sha": "3aa34b0d167958d9", "launches": 336, "dram_bytes_per_launch": 744630822},
+    "k_batch_test": {"src_sha": "3aa34b0d167958d9", "launches": 336, "dram_bytes_per_launch": 481128633},
 }
 
 
@@ -319,7 +320,9 @@ def run_ours(args, w, ws, rank, local):
     src = os.path.join(ROOT, "paper_1304_4661_gb300", "csrc",
                        "k_query.cu" if dom == "k_query" else "k_pruned.cu")
     prof = PROFILED.get(dom)
-    traffic = prof["dram_bytes_per_launch"] if prof and prof["src_sha"] == file_sha(src) else None
+    traffic = (prof["dram_bytes_per_launch"]
+               if prof and prof["src_sha"] == file_sha(src) and prof.get("launches") == kd["launches"]
+               else None)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": traffic,

@@ -67,8 +67,10 @@ typedef struct pll_index pll_index;
 typedef struct pll_build_opts {
     uint32_t t;          /* bit-parallel roots, 0..PLL_MAX_T (Sec. 5.4). */
     uint32_t root_batch; /* largest number of pruned-BFS roots processed in
-                            one batch; 0 = library schedule. Any value gives
-                            the same labels. */
+                            one batch (batches double from 64 up to it); 0 =
+                            16384, halved while n * root_batch / 8 bytes of
+                            visited bitmap would exceed 8 GiB. Any value
+                            gives the same labels. */
     uint32_t block;      /* threads per CTA of the pruned-BFS kernel: 128,
                             256, 512 or 1024; 0 = library default (256). */
     uint32_t flags;      /* reserved, must be 0. */
