@@ -10,10 +10,12 @@
 // d(r_i,t). Since the answer through {r_i} U S_{r_i} lies in [d~_i - 2, d~_i],
 // only roots with d~_i <= min_i d~_i + 1 can decide the minimum, and only
 // those whose d~_i - 2 beats the normal-label answer fetch their 16-byte mask
-// pairs. The normal labels are hub-sorted (hub ranks, Sec. 4.5.1); instead of
-// the sequential merge join of Sec. 3.3 each lane takes entries of the
-// shorter label and binary-searches the longer one, which finds the same
-// common hubs. No sentinel is needed (Sec. 4.5.2): bounds are explicit.
+// pairs. The normal labels are hub-sorted (hub ranks, Sec. 4.5.1): a warp
+// merges them 32 entries at a time (the merge join of Sec. 3.3, with the
+// comparisons of a window done by shuffles), or, when one label is much
+// longer, each lane takes entries of the shorter label and binary-searches the
+// longer one; both find the same common hubs. No sentinel is needed
+// (Sec. 4.5.2): bounds are explicit.
 #include <atomic>
 
 #include "pll_internal.cuh"
@@ -110,6 +112,54 @@ __device__ __forceinline__ uint32_t label_min(const QueryArgs &a, uint32_t s, ui
     return warp_min(best);
 }
 
+#ifndef PLL_MERGE_RATIO
+#define PLL_MERGE_RATIO 4
+#endif
+
+// min over common hubs of the two normal labels for one warp: a merge of the
+// hub-sorted labels 32 entries at a time (the merge join of Sec. 3.3 done by
+// a warp). Each lane holds one entry of the shorter label's window and finds
+// its hub in the other window by a 5-step search over the lanes (shuffles);
+// then the window whose last hub is smaller is passed whole and the other is
+// advanced past the hubs not above it, which can meet nothing that is left.
+// Labels read once, in coalesced 128-byte rows. When one label is more than
+// PLL_MERGE_RATIO times longer, binary searches of its entries (label_min)
+// touch less of it and are used instead.
+__device__ __forceinline__ uint32_t label_min_merge(const QueryArgs &a, uint32_t s, uint32_t t, int lane) {
+    const uint64_t os = a.lab_off[s], ot = a.lab_off[t];
+    const uint32_t ls = (uint32_t)(a.lab_off[s + 1] - os), lt = (uint32_t)(a.lab_off[t + 1] - ot);
+    const uint32_t la = ls <= lt ? ls : lt, lb = ls <= lt ? lt : ls;
+    if (la == 0) return BIG;
+    if (lb > PLL_MERGE_RATIO * la) return label_min(a, s, t, lane, 0, 32);
+    const uint32_t *A = a.lab + (ls <= lt ? os : ot);
+    const uint32_t *B = a.lab + (ls <= lt ? ot : os);
+    uint32_t best = BIG, ia = 0, ib = 0;
+    while (ia < la && ib < lb) {
+        const uint32_t na = min(32u, la - ia), nb = min(32u, lb - ib);
+        const bool va = (uint32_t)lane < na, vb = (uint32_t)lane < nb;
+        const uint32_t ea = va ? A[ia + lane] : NONE;  // padding sorts after every hub
+        const uint32_t eb = vb ? B[ib + lane] : NONE;
+        const uint32_t ha = entry_hub(ea), hb = entry_hub(eb);
+        // lower bound of ha in the window of B held across the lanes
+        uint32_t pos = 0;
+#pragma unroll
+        for (uint32_t stp = 16; stp > 0; stp >>= 1)
+            if (entry_hub(__shfl_sync(FULL, eb, pos + stp - 1)) < ha) pos += stp;
+        const uint32_t ep = __shfl_sync(FULL, eb, pos);
+        if (va && pos < nb && entry_hub(ep) == ha) best = min(best, entry_dist(ea) + entry_dist(ep));
+        const uint32_t lastA = entry_hub(__shfl_sync(FULL, ea, na - 1));
+        const uint32_t lastB = entry_hub(__shfl_sync(FULL, eb, nb - 1));
+        if (lastA <= lastB) {
+            ia += na;
+            ib += __popc(__ballot_sync(FULL, vb && hb <= lastA));
+        } else {
+            ib += nb;
+            ia += __popc(__ballot_sync(FULL, va && ha <= lastB));
+        }
+    }
+    return warp_min(best);
+}
+
 // The bit-parallel answer, fetching masks only where they can beat `best`
 // (the normal-label answer), then the final byte.
 __device__ __forceinline__ uint32_t finish_pair(const QueryArgs &a, uint32_t s, uint32_t t, int lane,
@@ -155,7 +205,7 @@ __global__ void __launch_bounds__(256) k_query(QueryArgs a) {
         }
         uint32_t td0, td1, dstar;
         bp_tilde(a, s, t, lane, &td0, &td1, &dstar);
-        const uint32_t best = finish_pair(a, s, t, lane, td0, td1, dstar, label_min(a, s, t, lane, 0, 32));
+        const uint32_t best = finish_pair(a, s, t, lane, td0, td1, dstar, label_min_merge(a, s, t, lane));
         if (lane == 0) store_answer(a, qi, best);
     }
 }
