@@ -424,11 +424,43 @@ PLL_API int pll_learned_order(const uint32_t *offsets, const uint32_t *cols, uin
                               uint64_t nnz, uint32_t t, const pll_mlp *mlp, uint32_t *order,
                               void *stream);
 
+/*
+ * The index as a file (the paper answers queries from a disk-resident index,
+ * Sec. 6; here the file is an image to keep and load, not to query in place).
+ *
+ * pll_save -- writes the index to `path` (created or truncated): a 48-byte
+ *   header (magic "PLLINDEX", version 1, n, t, row stride, graphs, a flag for
+ *   the batch graph array, nnz, label entries) followed by the device arrays
+ *   as they are (order, inverse order, bit-parallel distances and masks,
+ *   roots, graph of each rank for batch indices, label offsets, labels),
+ *   little-endian. PLL_E_INVAL if the file cannot be written. Synchronous.
+ * pll_load -- reads such a file into a new index on the current device.
+ *   Everything a query indexes with is checked first (the two orders are
+ *   inverse permutations, label offsets start at 0, never decrease and end
+ *   at the entry count); a file that fails, is truncated or has another
+ *   magic or version gives PLL_E_INVAL and no index. Build statistics other
+ *   than the sizes are zero. Synchronous.
+ */
+PLL_API int pll_save(const pll_index *idx, const char *path);
+PLL_API int pll_load(const char *path, pll_index **out);
+
 /* Build statistics (sizes, per-phase times in milliseconds). */
 PLL_API int pll_get_stats(const pll_index *idx, pll_stats *out);
 
 /* Release the index and its device memory. NULL is ignored. */
 PLL_API void pll_free(pll_index *idx);
+
+/*
+ * Test hooks for the allocation-failure paths; the paper has no counterpart.
+ * pll_test_fail_alloc(k): of the library's device and pinned host
+ *   allocations made by index builds, the next k succeed and the one after
+ *   fails as if the device were out of memory (the build then returns
+ *   PLL_E_NOMEM); k < 0 turns the hook off (the default). Process-wide.
+ * pll_test_live_allocs(): those allocations currently alive (an index holds
+ *   its own), so a failed build can be checked for leaks.
+ */
+PLL_API void pll_test_fail_alloc(int64_t k);
+PLL_API int64_t pll_test_live_allocs(void);
 
 /* Static, human-readable text for a status code. */
 PLL_API const char *pll_status_str(int status);

@@ -30,6 +30,7 @@ CU_SOURCES = [
     "pll_noalloc.cu",
     "pll_serve.cu",
     "k_learned.cu",
+    "pll_io.cu",
 ]
 
 

@@ -236,7 +236,7 @@ int bp_run(uint32_t n, uint32_t t, uint32_t graphs, const uint32_t *d_roff, cons
 
     PLL_CHECK(flag.alloc(4));
     uint32_t *h_flag = nullptr;
-    PLL_TRY(cudaMallocHost(&h_flag, 4));
+    PLL_TRY(host_malloc(&h_flag, 4));
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -261,7 +261,7 @@ int bp_run(uint32_t n, uint32_t t, uint32_t graphs, const uint32_t *d_roff, cons
         // "discovered" from the root then), so it is always processed
         if (*h_flag == 0 && L >= 1) break;
     }
-    cudaFreeHost(h_flag);
+    host_free(h_flag);
     if (st == PLL_OK) {
         k_bp_finish<<<(int)std::min<size_t>((nt + 255) / 256, (size_t)sms * 32), 256, 0, s>>>(
             nt, reinterpret_cast<ulonglong2 *>(d_bp_m));

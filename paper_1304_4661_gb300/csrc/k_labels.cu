@@ -209,7 +209,7 @@ int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s) {
     unsigned long long top = last_off + ((last_len + 3u) & ~3u);
     PLL_TRY(cudaMemcpyAsync(st.pool_top, &top, 8, cudaMemcpyHostToDevice, s));
     PLL_TRY(cudaStreamSynchronize(s));
-    cudaFree(st.pool);
+    dev_free(st.pool);
     st.pool = pool.as<uint32_t>();
     pool.release();
     st.pool_cap = new_cap;

@@ -19,6 +19,8 @@
 #include <new>
 #include <vector>
 
+#include <atomic>
+
 #include "pll_internal.cuh"
 
 namespace pll {
@@ -52,17 +54,17 @@ int bit_length(uint32_t x) {
 
 void free_index(pll_index *ix) {
     if (!ix) return;
-    cudaFree(ix->d_order);
-    cudaFree(ix->d_inv);
-    cudaFree(ix->d_bp_d);
-    cudaFree(ix->d_bp_m);
-    cudaFree(ix->d_bp_root);
-    cudaFree(ix->d_bp_cnt);
-    cudaFree(ix->d_bp_S);
-    cudaFree(ix->d_graph);
-    cudaFree(ix->d_lab_off);
-    cudaFree(ix->d_lab);
-    cudaFree(ix->d_qerr);
+    dev_free(ix->d_order);
+    dev_free(ix->d_inv);
+    dev_free(ix->d_bp_d);
+    dev_free(ix->d_bp_m);
+    dev_free(ix->d_bp_root);
+    dev_free(ix->d_bp_cnt);
+    dev_free(ix->d_bp_S);
+    dev_free(ix->d_graph);
+    dev_free(ix->d_lab_off);
+    dev_free(ix->d_lab);
+    dev_free(ix->d_qerr);
     delete ix;
 }
 
@@ -116,7 +118,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     st.pool_top = &d_ctr->pool_top;
     struct PoolGuard {
         LabelStore *st;
-        ~PoolGuard() { if (st->pool) cudaFree(st->pool); }
+        ~PoolGuard() { dev_free(st->pool); }
     } pool_guard{&st};
 
     int grid[2] = {0, 0};
@@ -155,10 +157,10 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         LevelDesc d;
     };
     Mirror *h = nullptr;
-    PLL_TRY(cudaMallocHost(&h, sizeof(Mirror)));
+    PLL_TRY(host_malloc(&h, sizeof(Mirror)));
     struct HostGuard {
         Mirror *h;
-        ~HostGuard() { cudaFreeHost(h); }
+        ~HostGuard() { host_free(h); }
     } host_guard{h};
     auto read_back = [&]() -> int {
         PLL_TRY(cudaMemcpyAsync(&h->c, d_ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, s));
@@ -317,8 +319,8 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     ix->entries = total;
 
     // step 4: compact CSR
-    PLL_TRY(cudaMalloc(&ix->d_lab_off, ((size_t)n + 1) * 8));
-    PLL_TRY(cudaMalloc(&ix->d_lab, std::max<uint64_t>(total, 1) * 4));
+    PLL_TRY(dev_malloc(&ix->d_lab_off, ((size_t)n + 1) * 8));
+    PLL_TRY(dev_malloc(&ix->d_lab, std::max<uint64_t>(total, 1) * 4));
     size_t ftb = 0;
     PLL_CHECK(labels_finalize(st, total, ix->d_lab_off, ix->d_lab, nullptr, &ftb, s));
     DevMem ftemp;
@@ -396,8 +398,8 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_CHECK(prep_validate_csr(g, d_err, s));
     PLL_CHECK(read_err(d_err, s, &h_err));
     if (h_err) return PLL_E_INVAL;
-    PLL_TRY(cudaMalloc(&ix->d_order, std::max<size_t>((size_t)n * 4, 4)));
-    PLL_TRY(cudaMalloc(&ix->d_inv, std::max<size_t>((size_t)n * 4, 4)));
+    PLL_TRY(dev_malloc(&ix->d_order, std::max<size_t>((size_t)n * 4, 4)));
+    PLL_TRY(dev_malloc(&ix->d_inv, std::max<size_t>((size_t)n * 4, 4)));
     DevMem m_gs, m_gof, m_local;
     if (batch) {  // each graph's own Degree order, graphs interleaved by local rank
         PLL_CHECK(m_gs.alloc(((size_t)graphs + 1) * 4));
@@ -424,12 +426,12 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_TRY(cudaMemsetAsync(m_inX.p, 0, std::max<size_t>(n, 1), s));
     const uint32_t t = o.t;
     const size_t gt = (size_t)graphs * t;
-    PLL_TRY(cudaMalloc(&ix->d_bp_root, std::max<size_t>(gt, 1) * 4));
-    PLL_TRY(cudaMalloc(&ix->d_bp_cnt, std::max<size_t>(gt, 1) * 4));
-    PLL_TRY(cudaMalloc(&ix->d_bp_S, std::max<size_t>(gt * BPW, 1) * 4));
+    PLL_TRY(dev_malloc(&ix->d_bp_root, std::max<size_t>(gt, 1) * 4));
+    PLL_TRY(dev_malloc(&ix->d_bp_cnt, std::max<size_t>(gt, 1) * 4));
+    PLL_TRY(dev_malloc(&ix->d_bp_S, std::max<size_t>(gt * BPW, 1) * 4));
     PLL_TRY(cudaMemsetAsync(ix->d_bp_S, 0xff, std::max<size_t>(gt * BPW, 1) * 4, s));
     if (batch) {
-        PLL_TRY(cudaMalloc(&ix->d_graph, std::max<size_t>((size_t)n * 4, 4)));
+        PLL_TRY(dev_malloc(&ix->d_graph, std::max<size_t>((size_t)n * 4, 4)));
         PLL_CHECK(prep_graph_by_rank(n, ix->d_order, m_gof.as<uint32_t>(), ix->d_graph, s));
     }
     if (batch)
@@ -449,8 +451,8 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     // ---- 2. bit-parallel labels
     tm.start();
     const size_t nt = (size_t)n * t;
-    PLL_TRY(cudaMalloc(&ix->d_bp_d, std::max<size_t>((size_t)n * ix->tp, 16)));
-    PLL_TRY(cudaMalloc(&ix->d_bp_m, std::max<size_t>(nt, 1) * 16));
+    PLL_TRY(dev_malloc(&ix->d_bp_d, std::max<size_t>((size_t)n * ix->tp, 16)));
+    PLL_TRY(dev_malloc(&ix->d_bp_m, std::max<size_t>(nt, 1) * 16));
     uint32_t bp_levels = 0;
     PLL_CHECK(bp_run(n, t, graphs, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), ix->d_bp_root,
                      ix->d_bp_cnt, ix->d_bp_S, ix->d_bp_d, ix->d_bp_m, d_err, s, &bp_levels));
@@ -468,7 +470,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
                            bmax, block, s));
     ix->stats.ms_pruned = tm.stop_ms();
 
-    PLL_TRY(cudaMalloc(&ix->d_qerr, 16));
+    PLL_TRY(dev_malloc(&ix->d_qerr, 16));
     PLL_TRY(cudaMemsetAsync(ix->d_qerr, 0, 16, s));
     PLL_TRY(cudaStreamSynchronize(s));
     ix->stats.index_bytes = (uint64_t)n * 8 + (uint64_t)n * ix->tp + nt * 16 + ((uint64_t)n + 1) * 8 +
@@ -493,7 +495,16 @@ struct AsyncBuf {
 };
 
 int query_status(const pll_index *ix, cudaStream_t s) {
-    unsigned long long h[2] = {0, 0};
+    // the two counters come back into pinned memory (a pageable target makes
+    // the copy a staged one); one buffer per thread: pll_query is synchronous,
+    // so a thread has one in flight at a time. It lives as long as the thread.
+    static thread_local unsigned long long *pinned = nullptr;
+    unsigned long long stack_h[2] = {0, 0};
+    if (!pinned && cudaMallocHost(&pinned, 16) != cudaSuccess) {
+        (void)cudaGetLastError();
+        pinned = nullptr;
+    }
+    unsigned long long *h = pinned ? pinned : stack_h;
     PLL_TRY(cudaMemcpyAsync(h, ix->d_qerr, 16, cudaMemcpyDeviceToHost, s));
     PLL_TRY(cudaStreamSynchronize(s));
     if (h[0] == 0 && h[1] == 0) return PLL_OK;
@@ -503,6 +514,24 @@ int query_status(const pll_index *ix, cudaStream_t s) {
 }
 
 }  // namespace
+
+void index_release(pll_index *ix) { free_index(ix); }
+
+// allocation-failure test hook and live-allocation count
+static std::atomic<long long> g_fail_after{-1};
+static std::atomic<long long> g_live{0};
+
+bool alloc_should_fail() {
+    long long k = g_fail_after.load(std::memory_order_relaxed);
+    while (k >= 0) {
+        // k allocations still pass; the one that finds k == 0 fails and ends the countdown
+        if (g_fail_after.compare_exchange_weak(k, k - 1, std::memory_order_relaxed)) return k == 0;
+    }
+    return false;
+}
+
+void alloc_note(long long delta) { g_live.fetch_add(delta, std::memory_order_relaxed); }
+
 }  // namespace pll
 
 using namespace pll;
@@ -748,5 +777,9 @@ PLL_API int pll_get_stats(const pll_index *idx, pll_stats *out) {
 }
 
 PLL_API void pll_free(pll_index *idx) { free_index(idx); }
+
+PLL_API void pll_test_fail_alloc(int64_t k) { g_fail_after.store(k < 0 ? -1 : k); }
+
+PLL_API int64_t pll_test_live_allocs(void) { return g_live.load(); }
 
 }  // extern "C"

@@ -77,6 +77,7 @@ namespace pll {
 
 // ---- host helpers (pll_abi.cu) ----
 int cuda_status(cudaError_t e);  // maps a CUDA error to a pll_status
+void index_release(pll_index *ix);  // frees every device array and the index
 
 #define PLL_TRY(expr)                                   \
     do {                                                \
@@ -90,7 +91,38 @@ int cuda_status(cudaError_t e);  // maps a CUDA error to a pll_status
         if (_s != PLL_OK) return _s; \
     } while (0)
 
-// Device allocation that frees itself; release() hands ownership out.
+// Every device and pinned allocation of the build goes through these: they
+// keep a count of live allocations and carry the allocation-failure test
+// hook (pll_test_fail_alloc), both kept in pll_abi.cu.
+bool alloc_should_fail();
+void alloc_note(long long delta);
+template <class T> inline cudaError_t dev_malloc(T **p, size_t b) {
+    *p = nullptr;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), b);
+    if (e == cudaSuccess) alloc_note(1);
+    return e;
+}
+inline void dev_free(void *p) {
+    if (!p) return;
+    cudaFree(p);
+    alloc_note(-1);
+}
+template <class T> inline cudaError_t host_malloc(T **p, size_t b) {
+    *p = nullptr;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(p), b);
+    if (e == cudaSuccess) alloc_note(1);
+    return e;
+}
+inline void host_free(void *p) {
+    if (!p) return;
+    cudaFreeHost(p);
+    alloc_note(-1);
+}
+
+// Device allocation that frees itself; release() hands ownership out (the
+// new owner frees it with dev_free).
 struct DevMem {
     void *p = nullptr;
     size_t bytes = 0;
@@ -101,13 +133,13 @@ struct DevMem {
     int alloc(size_t b) {
         reset();
         if (b == 0) b = 16;
-        cudaError_t e = cudaMalloc(&p, b);
+        cudaError_t e = dev_malloc(&p, b);
         if (e != cudaSuccess) { p = nullptr; (void)cudaGetLastError(); return PLL_E_NOMEM; }
         bytes = b;
         return PLL_OK;
     }
     void reset() {
-        if (p) cudaFree(p);
+        dev_free(p);
         p = nullptr;
         bytes = 0;
     }

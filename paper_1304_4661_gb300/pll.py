@@ -30,6 +30,7 @@ SYMBOLS = [
     "pll_features", "pll_hub_counts", "pll_order_from_scores", "pll_mlp_create", "pll_mlp_free",
     "pll_mlp_set_params", "pll_mlp_get_params", "pll_mlp_forward", "pll_mlp_grad",
     "pll_mlp_read_grad", "pll_mlp_adam", "pll_mlp_train_step", "pll_learned_order",
+    "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs",
 ]
 MLP_NPARAM = 4801
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -156,6 +157,14 @@ def load(build_if_missing: bool = True):
         f.argtypes = args
     lib.pll_mlp_free.restype = None
     lib.pll_mlp_free.argtypes = [vp]
+    lib.pll_save.restype = i32
+    lib.pll_save.argtypes = [vp, C.c_char_p]
+    lib.pll_load.restype = i32
+    lib.pll_load.argtypes = [C.c_char_p, pp]
+    lib.pll_test_fail_alloc.restype = None
+    lib.pll_test_fail_alloc.argtypes = [C.c_int64]
+    lib.pll_test_live_allocs.restype = C.c_int64
+    lib.pll_test_live_allocs.argtypes = []
     _lib = lib
     return lib
 
@@ -332,6 +341,21 @@ class Index:
         c = C.c_uint64(0)
         _check(load().pll_label_entries(self._h, C.byref(c)), "pll_label_entries")
         return int(c.value)
+
+    def save(self, path):
+        """pll_save: write the index to a file."""
+        _check(load().pll_save(self._h, os.fsencode(path)), "pll_save")
+
+    @classmethod
+    def load(cls, path):
+        """pll_load: read an index written by save() onto the current device."""
+        h = C.c_void_p()
+        _check(load().pll_load(os.fsencode(path), C.byref(h)), "pll_load")
+        st = Stats()
+        _check(load().pll_get_stats(h.value, C.byref(st)), "pll_get_stats")
+        ix = cls(h.value, int(st.n), int(st.t))
+        ix.graphs = max(int(st.graphs), 1)
+        return ix
 
     def hub_counts(self, stream=None):
         """pll_hub_counts: (counts int32 CUDA [n], log1p(counts) float32 CUDA [n])."""
