@@ -36,18 +36,48 @@ __device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t *__restrict__
     return lo;
 }
 
-__global__ void k_cleanup(const uint64_t *__restrict__ T, uint64_t P, uint8_t *keep) {
+// Tuples of vertex v_k with hub < k, for every root k of the batch: their
+// range [seg[2 (k - k0)], seg[2 (k - k0) + 1]) in the sorted tuples, found once
+// per root instead of once per tuple.
+__global__ void k_root_segments(const uint64_t *__restrict__ T, uint64_t P, uint32_t k0, uint32_t B,
+                                uint64_t *seg) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const uint32_t k = k0 + i;
+    const uint64_t lo = lower_bound_u64(T, 0, P, (uint64_t)k << 32);
+    seg[2 * i] = lo;
+    seg[2 * i + 1] = lower_bound_u64(T, lo, P, pack_tuple(k, k, 0));
+}
+
+// Tuple x = (u, k, d) is surplus iff some in-batch hub h < k has (u, h, a)
+// and (v_k, h, b) with a + b <= d (the lowest such h lies on a shortest
+// v_k-u path). u's tuples with hub < k are [lo_u, x): the run of u ends at x,
+// and its start is found by galloping back from x (runs are short). v_k's
+// come from seg (or, without it, a binary search).
+__global__ void k_cleanup(const uint64_t *__restrict__ T, uint64_t P, const uint64_t *__restrict__ seg,
+                          uint32_t k0, uint8_t *keep) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t key = T[x];
         const uint32_t u = (uint32_t)(key >> 32);
         const uint32_t e = (uint32_t)key;
         const uint32_t k = entry_hub(e), d = entry_dist(e);
-        // tuples of u with hub < k: [lo_u, x)
-        const uint64_t lo_u = lower_bound_u64(T, 0, x, (uint64_t)u << 32);
-        // tuples of v_k with hub < k: [lo_k, hi_k)
-        const uint64_t lo_k = lower_bound_u64(T, 0, P, (uint64_t)k << 32);
-        const uint64_t hi_k = lower_bound_u64(T, lo_k, P, pack_tuple(k, k, 0));
+        // start of u's run: gallop back while the entry is still u's, then
+        // search the last step
+        uint64_t b = x, stp = 1;
+        while (b >= stp && (uint32_t)(T[b - stp] >> 32) == u) {
+            b -= stp;
+            stp <<= 1;
+        }
+        const uint64_t lo_u = lower_bound_u64(T, b >= stp ? b - stp : 0, b, (uint64_t)u << 32);
+        uint64_t lo_k, hi_k;
+        if (seg) {
+            lo_k = seg[2 * (k - k0)];
+            hi_k = seg[2 * (k - k0) + 1];
+        } else {
+            lo_k = lower_bound_u64(T, 0, P, (uint64_t)k << 32);
+            hi_k = lower_bound_u64(T, lo_k, P, pack_tuple(k, k, 0));
+        }
         uint64_t i = lo_u, j = lo_k;
         bool drop = false;
         while (i < x && j < hi_k) {
@@ -141,9 +171,16 @@ int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int end_
     return PLL_OK;
 }
 
-int labels_cleanup(const uint64_t *d_sorted, uint64_t count, uint8_t *d_keep, cudaStream_t s) {
+int labels_cleanup(const uint64_t *d_sorted, uint64_t count, uint8_t *d_keep, uint32_t k0, uint32_t B,
+                   void *scratch, size_t scratch_bytes, cudaStream_t s) {
     if (count == 0) return PLL_OK;
-    k_cleanup<<<grid_for(count, 256), 256, 0, s>>>(d_sorted, count, d_keep);
+    uint64_t *seg = nullptr;
+    if (scratch && scratch_bytes >= (size_t)B * 16) {
+        seg = static_cast<uint64_t *>(scratch);
+        k_root_segments<<<(B + 255) / 256, 256, 0, s>>>(d_sorted, count, k0, B, seg);
+        PLL_TRY(cudaGetLastError());
+    }
+    k_cleanup<<<grid_for(count, 256), 256, 0, s>>>(d_sorted, count, seg, k0, d_keep);
     PLL_TRY(cudaGetLastError());
     return PLL_OK;
 }

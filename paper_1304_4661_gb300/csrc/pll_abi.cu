@@ -293,7 +293,9 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             size_t tb = temp_bytes;
             PLL_CHECK(labels_sort_tuples(m_out.as<uint64_t>(), m_sorted.as<uint64_t>(), P, end_bit,
                                          m_temp.p, &tb, s));
-            PLL_CHECK(labels_cleanup(m_sorted.as<uint64_t>(), P, m_keep.as<uint8_t>(), s));
+            // the sort is done with the temporary space; the cleanup borrows it
+            PLL_CHECK(labels_cleanup(m_sorted.as<uint64_t>(), P, m_keep.as<uint8_t>(), k0, k1 - k0,
+                                     m_temp.p, temp_bytes, s));
             tb = temp_bytes;
             PLL_CHECK(labels_compact(m_sorted.as<uint64_t>(), m_keep.as<uint8_t>(), P,
                                      m_out.as<uint64_t>(), &d_ctr->nkept, m_temp.p, &tb, s));

@@ -260,7 +260,9 @@ struct LabelStore {
 };
 int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int end_bit,
                        void *d_temp, size_t *temp_bytes, cudaStream_t s);
-int labels_cleanup(const uint64_t *d_sorted, uint64_t count, uint8_t *d_keep, cudaStream_t s);
+// scratch (>= 16 B bytes, may be NULL) holds each root's own tuple range
+int labels_cleanup(const uint64_t *d_sorted, uint64_t count, uint8_t *d_keep, uint32_t k0, uint32_t B,
+                   void *scratch, size_t scratch_bytes, cudaStream_t s);
 int labels_compact(const uint64_t *d_in, const uint8_t *d_keep, uint64_t count, uint64_t *d_out,
                    unsigned long long *d_nout, void *d_temp, size_t *temp_bytes, cudaStream_t s);
 int labels_append(const LabelStore &st, const uint64_t *d_kept,
