@@ -47,8 +47,8 @@ WORKLOADS = {
 PROFILED = {
     # ncu, all 336 + 336 sweep launches of one R-MAT-20 build at the default
     # root batch (profiles/k_batch_sweeps_rmat20.md); valid for that launch count
-    "k_batch_expand": {"src_sha": "3aa34b0d167958d9", "launches": 336, "dram_bytes_per_launch": 744630822},
-    "k_batch_test": {"src_sha": "3aa34b0d167958d9", "launches": 336, "dram_bytes_per_launch": 481128633},
+    "k_batch_expand": {"src_sha": "671715a06e81c3ac", "launches": 336, "dram_bytes_per_launch": 772327190},
+    "k_batch_test": {"src_sha": "671715a06e81c3ac", "launches": 336, "dram_bytes_per_launch": 484422056},
 }
 
 
