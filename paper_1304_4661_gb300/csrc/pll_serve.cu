@@ -51,7 +51,8 @@ struct Request {
     uint8_t *out = nullptr;
     Clock::time_point t_submit;
     double latency_us = 0;
-    bool staged = false, done = false;
+    std::atomic<bool> staged{false};  // set by the client once its pairs are in place
+    bool done = false;
     int status = PLL_OK;
 };
 
@@ -97,6 +98,8 @@ struct pll_server {
     bool stop = false;
     std::thread worker;
     pll_server_stats st{};
+    std::atomic<unsigned long long> pack_ns{0};  // client staging time (no lock)
+    std::atomic<uint64_t> staged_seq{0};         // bumped by every staged request
     int fatal = PLL_OK;
 };
 
@@ -171,6 +174,8 @@ void worker_loop(pll_server *sv) {
     // condition variable: a thread woken from sleep adds tens of microseconds
     constexpr int SPIN_US = 1000;
     Clock::time_point last_work = Clock::now();
+    uint64_t seen_seq = ~0ull;  // staged_seq at the last look under the lock
+    bool leftover = false;
     for (;;) {
         // 1. retire finished runs, oldest first
         while (!sv->inflight.empty()) {
@@ -192,10 +197,18 @@ void worker_loop(pll_server *sv) {
             if (!sv->slots[i].busy) { slot = (int)i; break; }
         Run run;
         bool quit = false;
-        {
+        // the lock is taken only when a run could be launched (a slot is free
+        // and requests were staged since the last look, or some were left
+        // over) or when nothing is in flight (to sleep or to stop); otherwise
+        // the loop just polls the runs in flight, leaving the lock to clients
+        const uint64_t seq = sv->staged_seq.load(std::memory_order_acquire);
+        const bool look = sv->inflight.empty() || (slot >= 0 && (seq != seen_seq || leftover));
+        if (look) {
+            seen_seq = seq;
             std::unique_lock<std::mutex> lock(sv->mu);
             auto ready = [sv] {
-                return sv->nlaunched < sv->live.size() && sv->live[sv->nlaunched]->staged;
+                return sv->nlaunched < sv->live.size() &&
+                       sv->live[sv->nlaunched]->staged.load(std::memory_order_acquire);
             };
             if (!ready() && sv->inflight.empty()) {
                 if (sv->stop && sv->live.empty()) quit = true;
@@ -207,7 +220,8 @@ void worker_loop(pll_server *sv) {
                 run.off = sv->live[sv->nlaunched]->off;
                 for (size_t i = sv->nlaunched; i < sv->live.size(); ++i) {
                     Request *q = sv->live[i];
-                    if (!q->staged || q->off != run.off + run.pairs) break;  // not staged, or wrapped
+                    if (!q->staged.load(std::memory_order_acquire) || q->off != run.off + run.pairs)
+                        break;  // not staged, or wrapped
                     if (!run.reqs.empty() && run.pairs + q->q > sv->opts.max_batch_pairs) break;
                     run.reqs.push_back(q);
                     run.pairs += q->q;
@@ -218,6 +232,7 @@ void worker_loop(pll_server *sv) {
                 sv->st.batches++;
                 sv->st.max_batch_pairs = std::max(sv->st.max_batch_pairs, run.pairs);
             }
+            leftover = ready();  // staged requests the run did not take (size, wrap)
         }
         if (quit) return;
         if (run.slot >= 0) {
@@ -321,8 +336,11 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
         if (sv->stop) { delete r; return PLL_E_INVAL; }
         r->off = off;
         r->ticket = sv->next_ticket++;
+        sv->table[r->ticket] = r;
         sv->live.push_back(r);
         sv->st.max_inflight_bytes = std::max(sv->st.max_inflight_bytes, 9 * ring_used(sv->live, sv->P));
+        sv->st.requests++;
+        sv->st.pairs += q;
     }
     // stage the pairs into the request's own slots, checking the ids on the way
     const Clock::time_point t0 = Clock::now();
@@ -336,15 +354,14 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
         h[2 * i + 1] = b < n ? b : 0;
     }
     const uint64_t tk = r->ticket;
-    {
+    if (bad) {  // keeps its slots until its run retires, answers nobody
         std::lock_guard<std::mutex> lock(sv->mu);
-        if (bad) r->ticket = 0;  // keeps its slots until its run retires, answers nobody
-        else sv->table[tk] = r;
-        r->staged = true;
-        sv->st.requests++;
-        sv->st.pairs += q;
-        sv->st.pack_us += us_between(t0, Clock::now());
+        sv->table.erase(tk);
+        r->ticket = 0;
     }
+    sv->pack_ns.fetch_add((unsigned long long)(us_between(t0, Clock::now()) * 1e3), std::memory_order_relaxed);
+    r->staged.store(true, std::memory_order_release);  // pairs and ticket before the flag
+    sv->staged_seq.fetch_add(1, std::memory_order_release);
     sv->cv_work.notify_one();
     if (bad) return PLL_E_INVAL;
     *ticket = tk;
@@ -428,6 +445,7 @@ PLL_API int pll_server_get_stats(pll_server *sv, pll_server_stats *out) {
     if (!sv || !out) return PLL_E_INVAL;
     std::lock_guard<std::mutex> lock(sv->mu);
     *out = sv->st;
+    out->pack_us = sv->pack_ns.load(std::memory_order_relaxed) / 1e3;
     return PLL_OK;
 }
 
