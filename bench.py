@@ -127,13 +127,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def dist_setup():
+def dist_setup(backend=None):
+    """One process per GPU, launched by torchrun (RANK / WORLD_SIZE /
+    MASTER_* from the environment). Every rank runs an independent replica
+    of the workload; ranks meet only in barriers and in the reduction of
+    their timings. NCCL with GPUs, gloo without (the CPU tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -143,14 +150,31 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(ws, x):
+def _reduce(ws, x, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(ws, x):
+    import torch.distributed as dist
+    return _reduce(ws, x, dist.ReduceOp.MAX) if ws > 1 else x
+
+
+def sum_over_ranks(ws, x):
+    import torch.distributed as dist
+    return _reduce(ws, x, dist.ReduceOp.SUM) if ws > 1 else x
+
+
+def job_rate(ws, units, seconds):
+    """Whole-job throughput: the units every rank processed over the time
+    of the slowest rank."""
+    return sum_over_ranks(ws, units) / max_over_ranks(ws, seconds)
 
 
 # ---------------------------------------------------------------- our arm
@@ -213,6 +237,7 @@ def run_ours(args, w, ws, rank, local):
     build_ms = statistics.mean(r[0] for r in recs)
     query_ms = statistics.mean(r[1] for r in recs)
     step_ms = build_ms + query_ms
+    queries_per_s = job_rate(ws, w["queries"], query_ms * 1e-3)
     build_ms = max_over_ranks(ws, build_ms)
     step_ms = max_over_ranks(ws, step_ms)
     st = recs[-1][2]
@@ -338,7 +363,7 @@ def run_ours(args, w, ws, rank, local):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": describe(w, g),
         "build_s": round(build_ms / 1e3, 6),
-        "queries_per_s": round(q / (query_ms * 1e-3), 1),
+        "queries_per_s": round(queries_per_s, 1),
         "query_kernel_ms": round(qk_ms, 3),
         "query_p50_us": round(p50, 2), "query_p99_us": round(p99, 2),
         "latency_note": "per single-pair synchronous pll_query call, host wall clock",
