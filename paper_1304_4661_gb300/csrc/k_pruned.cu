@@ -227,12 +227,14 @@ __device__ __forceinline__ bool quick_masks(const BatchArgs &a, uint32_t k, uint
 }
 
 // entries [lvl_b, lvl_e) of the current level -> candidates of the next
-// 1024 threads per SM (64 registers a thread): 50% occupancy; with the
-// registers it would take otherwise (72) only 768 threads fit, and the sweep,
-// bound by the latency of its claims and row loads, ran 12% slower
+// 1280 threads per SM (48 registers a thread): the sweep is bound by the
+// latency of its claims and row loads, so resident warps pay: at 72 registers
+// (768 threads) it ran 14% slower than here. The root's distance row, the same
+// for every lane of a warp, sits once per warp in shared memory.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_batch_expand(BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs a) {
     const int lane = threadIdx.x & 31;
+    __shared__ uint4 s_kr[BLOCK / 32][PLL_MAX_T / 16];
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
     const uint32_t level = a.desc->level;
@@ -243,12 +245,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_batch_expand(BatchArgs 
         const uint32_t k = entry_hub((uint32_t)key);
         const uint32_t slot = k - a.k0;
         const uint32_t sw = slot >> 5, sbit = 1u << (slot & 31);
-        // the root's distance row, kept in registers for every lane
-        uint4 kr[PLL_MAX_T / 16];
-#pragma unroll
-        for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
-            kr[c] = (c < (a.tp >> 4)) ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp) + c)
-                                      : make_uint4(~0u, ~0u, ~0u, ~0u);
+        // the root's distance row, one copy per warp
+        uint4 (&kr)[PLL_MAX_T / 16] = s_kr[threadIdx.x >> 5];
+        __syncwarp();  // the previous entry's tests are done with it
+        if (lane < PLL_MAX_T / 16)
+            kr[lane] = ((uint32_t)lane < (a.tp >> 4))
+                           ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp) + lane)
+                           : make_uint4(~0u, ~0u, ~0u, ~0u);
+        __syncwarp();
         const uint32_t eb = a.roff[u], ee = a.roff[u + 1];
         nexp += ee - eb;
         for (uint32_t x = eb; x < ee; x += 32) {
