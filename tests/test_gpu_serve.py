@@ -130,3 +130,18 @@ def test_concurrent_clients(served):
     assert not errors, errors
     assert np.array_equal(np.concatenate(got), expect)
     assert st["requests"] == len(off) - 1
+
+
+def test_wait_timeout_keeps_the_ticket(served):
+    """A wait that runs out returns PLL_E_TIMEOUT and leaves the ticket valid;
+    the next wait delivers the answer."""
+    g, ix, ref = served
+    s, t = gg.pairs(g.n, 1_000_000, 31)
+    with pll.Server(ix) as sv:
+        tk = sv.submit(s, t)
+        with pytest.raises(TimeoutError):
+            sv.wait(tk, timeout_us=0)
+        d, lat = sv.wait(tk)
+    assert lat > 0
+    sample = np.arange(0, len(s), 997)
+    assert np.array_equal(d[sample], ref.query_batch(s[sample], t[sample]))
