@@ -140,6 +140,8 @@ def dist_setup(backend=None):
         import torch.distributed as dist
         if backend is None:
             backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)  # each rank's communicator on its own GPU
         dist.init_process_group(backend)
     return ws, rank, local
 
