@@ -194,3 +194,26 @@ def test_query_launch_sizes(t):
         assert got[q // 2] == 255
         keep = np.arange(q) != q // 2
         assert np.array_equal(got[keep], expect[keep]), q
+
+
+def test_size_and_distance_limits():
+    """n must stay below 2^24 (hub ranks are packed into 24 bits): n = 2^24 is
+    PLL_E_RANGE before any memory is read. A path of 255 vertices has the
+    largest finite 8-bit distance, 254, between its ends; it is answered
+    exactly (255 vertices is the longest path the labels can hold)."""
+    import torch
+    from paper_1304_4661_gb300 import pll
+    off = torch.zeros((1 << 24) + 1, dtype=torch.int32, device="cuda")
+    col = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(pll.PLLError) as e:
+        pll.Index.build(off, col[:0], t=0)
+    assert e.value.code == pll.PLL_E_RANGE
+    del off
+    p = graphs.path(255)
+    for t in (0, 2):
+        ix, ref = check_index(p, t)
+        s = np.array([0, 254, 0, 127], dtype=np.uint32)
+        u = np.array([254, 0, 127, 254], dtype=np.uint32)
+        got = gpu_query(ix, s, u)
+        assert got.tolist() == [254, 254, 127, 127]
+        assert np.array_equal(got, ref.query_batch(s, u))
