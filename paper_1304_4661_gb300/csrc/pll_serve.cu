@@ -60,6 +60,7 @@ struct Run {
     std::vector<Request *> reqs;  // consecutive in the ring
     uint64_t off = 0, pairs = 0;
     int slot = -1;
+    int fail = PLL_OK;  // a launch that failed: retired with this status, in order
 };
 
 struct Slot {
@@ -180,6 +181,11 @@ void worker_loop(pll_server *sv) {
         // 1. retire finished runs, oldest first
         while (!sv->inflight.empty()) {
             const Run &r = sv->inflight.front();
+            if (r.fail != PLL_OK) {  // its event was never recorded
+                retire_run(sv, r, r.fail);
+                sv->inflight.pop_front();
+                continue;
+            }
             const Slot &sl = sv->slots[r.slot];
             const cudaError_t e = cudaEventQuery(sl.done);
             if (e == cudaErrorNotReady) break;
@@ -237,11 +243,13 @@ void worker_loop(pll_server *sv) {
         if (quit) return;
         if (run.slot >= 0) {
             const int s = launch_run(sv, run);
-            if (s != PLL_OK) {  // nothing of the run is in flight once the stream drains
+            if (s != PLL_OK) {
+                // nothing of the run is in flight once the stream drains; it
+                // retires behind the runs launched before it (requests leave
+                // the ring in order)
                 cudaStreamSynchronize(sv->slots[run.slot].stream);
                 sv->fatal = s;
-                retire_run(sv, run, s);
-                continue;
+                run.fail = s;
             }
             sv->inflight.push_back(std::move(run));
             last_work = Clock::now();
