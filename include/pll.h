@@ -388,9 +388,11 @@ PLL_API int pll_server_stop(pll_server *sv);
  *   pll_mlp_forward     y[i] = score of row i of x (device float[n][8]).
  *   pll_mlp_grad        gradient of the mean squared error over the batch
  *                       (row g = x[idx[g]] with target[idx[g]], or row g if
- *                       idx is NULL; idx device uint32[batch]) with respect to
- *                       the bf16 parameters, kept on the device with the loss;
- *                       deterministic. PLL_E_RANGE if batch > max_batch.
+ *                       idx is NULL; idx device uint32[batch], every entry
+ *                       a row of x and target -- not checked, as x's length
+ *                       is not passed) with respect to the bf16 parameters,
+ *                       kept on the device with the loss; deterministic.
+ *                       PLL_E_RANGE if batch > max_batch.
  *   pll_mlp_read_grad   gradient (host float[4801]) and/or loss (host float).
  *                       Synchronous.
  *   pll_mlp_adam        one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias
