@@ -67,7 +67,7 @@ def build_graphgen(force: bool = False) -> str:
 
 
 def pll_sources():
-    hdrs = sorted(CSRC.glob("*.cuh")) + sorted(INCLUDE.glob("*.h"))
+    hdrs = sorted(CSRC.glob("*.cuh")) + sorted(CSRC.glob("*.h")) + sorted(INCLUDE.glob("*.h"))
     return [CSRC / s for s in CU_SOURCES], hdrs
 
 

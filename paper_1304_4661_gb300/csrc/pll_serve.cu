@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "pll_internal.cuh"
+#include "serve_ring.h"
 
 namespace {
 
@@ -106,22 +107,11 @@ struct pll_server {
 
 namespace {
 
-// First-fit allocation in the FIFO ring. The live requests hold, in order,
-// one run of slots [front.off, back end), or two once the ring has wrapped
-// (back.off < front.off); the slots skipped at the end when a request wraps
-// to 0 are free again once the requests before them retire.
+// Slots for q pairs in the FIFO ring of live requests (serve_ring.h).
 bool ring_alloc(const std::deque<Request *> &live, uint64_t cap, uint64_t q, uint64_t *off) {
-    if (q > cap) return false;
-    if (live.empty()) { *off = 0; return true; }
-    const uint64_t first = live.front()->off;
-    const uint64_t end = live.back()->off + live.back()->q;
-    if (live.back()->off >= first) {  // not wrapped: free [end, cap) and [0, first)
-        if (cap - end >= q) { *off = end; return true; }
-        if (first >= q) { *off = 0; return true; }
-        return false;
-    }
-    if (first - end >= q) { *off = end; return true; }  // wrapped: free [end, first)
-    return false;
+    if (live.empty()) return pll::ring_place(true, 0, 0, 0, cap, q, off);
+    return pll::ring_place(false, live.front()->off, live.back()->off, live.back()->off + live.back()->q,
+                           cap, q, off);
 }
 
 uint64_t ring_used(const std::deque<Request *> &live, uint64_t cap) {
