@@ -8,8 +8,9 @@ imports the product: the two meet only through the seeded inputs.
 ``oracle.c`` is a plain single-threaded C restatement of the paper:
 the Degree order (Sec. 4.4.2), bit-parallel labels (Alg. 3, Sec. 5),
 the pruned BFSs of Alg. 1/2 with bit-parallel pruning (Sec. 5.4), the
-label query (Sec. 3.3, Sec. 5.3), plain BFS, and the closed form of one
-label derived from Thm 4.1 / Thm 4.2 (see the header of oracle.c).
+label query (Sec. 3.3, Sec. 5.3), plain BFS, the closed form of one
+label derived from Thm 4.1 / Thm 4.2, and the parents and path restoration
+of the shortest-path queries of Sec. 6 (see the header of oracle.c).
 """
 from __future__ import annotations
 
@@ -72,6 +73,10 @@ def _load():
         lib.orc_export_bp.argtypes = [vp, vp, vp, vp]
         lib.orc_export_bp_roots.restype = None
         lib.orc_export_bp_roots.argtypes = [vp, vp, vp, vp]
+        lib.orc_export_parents.restype = None
+        lib.orc_export_parents.argtypes = [vp, vp]
+        lib.orc_path.restype = C.c_long
+        lib.orc_path.argtypes = [vp, vp, vp, u32, u32, vp]
         lib.orc_export_order.restype = None
         lib.orc_export_order.argtypes = [vp, vp]
         lib.orc_counters.restype = None
@@ -180,6 +185,25 @@ class Index:
         dists = np.empty(max(tot, 1), dtype=np.uint8)
         lib.orc_export_labels(self._h, off.ctypes.data, hubs.ctypes.data, dists.ctypes.data)
         return Labels(off, hubs[:tot], dists[:tot])
+
+    def parents(self) -> np.ndarray:
+        """Parent of each label entry in its hub's pruned BFS tree (Sec. 6),
+        vertex ids, in the layout of labels()."""
+        lib = _load()
+        tot = lib.orc_total_entries(self._h)
+        out = np.empty(max(tot, 1), dtype=np.uint32)
+        lib.orc_export_parents(self._h, out.ctypes.data)
+        return out[:tot]
+
+    def path(self, s: int, u: int) -> np.ndarray:
+        """One shortest s-u path (vertex ids, s first) restored from the
+        labels and parents (Sec. 6); empty if u is unreachable."""
+        out = np.empty(256, dtype=np.uint32)
+        c = _load().orc_path(self._h, self._off.ctypes.data, self._col.ctypes.data, s, u,
+                             out.ctypes.data)
+        if c < 0:
+            raise OracleError(-c, "path")
+        return out[:c].copy()
 
     def bp(self):
         nt = max(self.n * self.t, 1)

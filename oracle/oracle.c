@@ -30,6 +30,19 @@
  *                         pruning (Sec. 5.4). One BFS from u with a dynamic
  *                         program over shortest-path predecessors.
  *
+ *   orc_export_parents -- Sec. 6, "Shortest-Path Queries": each label entry
+ *                         (u, d) of L(v) also carries the parent of v in the
+ *                         pruned BFS tree rooted at u (the vertex whose
+ *                         expansion first reached v; u itself for (u, 0)).
+ *   orc_path           -- one shortest s-t path restored from the labels: the
+ *                         best common hub h of L(s) and L(t), then the tree of
+ *                         h climbed from s and from t through those parents.
+ *                         When only the bit-parallel label reaches the
+ *                         distance, the path goes through r_i or a member of
+ *                         S_{r_i}, whose distance to every vertex the label
+ *                         gives exactly (Sec. 5.1); each step moves to the
+ *                         first neighbour one hop nearer.
+ *
  *   orc_core_numbers   -- core number of every vertex (the largest k such that
  *                         the vertex lies in a subgraph of minimum degree k),
  *                         one of the vertex features of the learned order; the
@@ -81,6 +94,7 @@ typedef struct orc_index {
     uint32_t *len, *cap;
     uint32_t **hub;
     uint8_t **dist;
+    uint32_t **par;     /* parent of the vertex in the hub's pruned BFS tree (Sec. 6) */
     /* counters of the work done by the pruned BFSs */
     uint64_t visited, labeled, scanned, labeled_deg;
 } orc_index;
@@ -141,7 +155,7 @@ int orc_bfs(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t src, 
     return st;
 }
 
-static int label_push(orc_index *ix, uint32_t u, uint32_t hub_rank, uint8_t d) {
+static int label_push(orc_index *ix, uint32_t u, uint32_t hub_rank, uint8_t d, uint32_t parent) {
     if (ix->len[u] == ix->cap[u]) {
         uint32_t nc = ix->cap[u] ? 2 * ix->cap[u] : 4;
         uint32_t *h = (uint32_t *)realloc(ix->hub[u], (size_t)nc * sizeof(uint32_t));
@@ -150,10 +164,14 @@ static int label_push(orc_index *ix, uint32_t u, uint32_t hub_rank, uint8_t d) {
         uint8_t *dd = (uint8_t *)realloc(ix->dist[u], nc);
         if (!dd) return ORC_E_NOMEM;
         ix->dist[u] = dd;
+        uint32_t *pp = (uint32_t *)realloc(ix->par[u], (size_t)nc * sizeof(uint32_t));
+        if (!pp) return ORC_E_NOMEM;
+        ix->par[u] = pp;
         ix->cap[u] = nc;
     }
     ix->hub[u][ix->len[u]] = hub_rank;
     ix->dist[u][ix->len[u]] = d;
+    ix->par[u][ix->len[u]] = parent;
     ix->len[u]++;
     return ORC_OK;
 }
@@ -264,7 +282,8 @@ static int bp_query(const orc_index *ix, uint32_t s, uint32_t u) {
 void orc_free(orc_index *ix) {
     if (!ix) return;
     if (ix->hub) for (uint32_t v = 0; v < ix->n; ++v) { free(ix->hub[v]); free(ix->dist[v]); }
-    free(ix->hub); free(ix->dist); free(ix->len); free(ix->cap);
+    if (ix->par) for (uint32_t v = 0; v < ix->n; ++v) free(ix->par[v]);
+    free(ix->hub); free(ix->dist); free(ix->par); free(ix->len); free(ix->cap);
     free(ix->order); free(ix->rank); free(ix->inX);
     free(ix->bp_root); free(ix->bp_cnt); free(ix->bp_S);
     free(ix->bp_d); free(ix->bp_m1); free(ix->bp_m0);
@@ -294,8 +313,10 @@ orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
     ix->cap = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
     ix->hub = (uint32_t **)calloc((size_t)n + 1, sizeof(uint32_t *));
     ix->dist = (uint8_t **)calloc((size_t)n + 1, sizeof(uint8_t *));
+    ix->par = (uint32_t **)calloc((size_t)n + 1, sizeof(uint32_t *));
     if (!ix->order || !ix->rank || !ix->inX || !ix->bp_root || !ix->bp_cnt || !ix->bp_S ||
-        !ix->bp_d || !ix->bp_m1 || !ix->bp_m0 || !ix->len || !ix->cap || !ix->hub || !ix->dist) {
+        !ix->bp_d || !ix->bp_m1 || !ix->bp_m0 || !ix->len || !ix->cap || !ix->hub || !ix->dist ||
+        !ix->par) {
         orc_free(ix); *status = ORC_E_NOMEM; return NULL;
     }
     /* the vertex order v_1..v_n (Sec. 4.4) */
@@ -330,8 +351,9 @@ orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
     if (with_pruned) {
         uint8_t *T = (uint8_t *)malloc((size_t)n + 1);     /* root array T (Sec. 4.5.1) */
         uint8_t *Pd = (uint8_t *)malloc((size_t)n + 1);    /* tentative distances P */
+        uint32_t *Pp = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t)); /* BFS-tree parents */
         uint32_t *visited = Q1;                            /* for the lazy reset */
-        if (!T || !Pd) { free(T); free(Pd); st = ORC_E_NOMEM; goto done; }
+        if (!T || !Pd || !Pp) { free(T); free(Pd); free(Pp); st = ORC_E_NOMEM; goto done; }
         memset(T, INF8, n);
         memset(Pd, INF8, n);
         for (uint32_t k = 0; k < n && st == ORC_OK; ++k) {
@@ -341,6 +363,7 @@ orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
             uint32_t head = 0, tail = 0;
             Q0[tail++] = vk;
             Pd[vk] = 0;
+            Pp[vk] = vk;
             while (head < tail) {
                 uint32_t u = Q0[head++];
                 int delta = Pd[u];
@@ -356,7 +379,7 @@ orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
                 }
                 if (pruned) continue;
                 /* L'_k[u] <- L'_{k-1}[u] U {(v_k, P[u])}, hub stored as rank k */
-                if ((st = label_push(ix, u, k, (uint8_t)delta))) break;
+                if ((st = label_push(ix, u, k, (uint8_t)delta, Pp[u]))) break;
                 ix->labeled++;
                 ix->labeled_deg += off[u + 1] - off[u];
                 for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
@@ -364,6 +387,7 @@ orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
                     if (Pd[w] != INF8) continue;
                     if (delta + 1 >= INF8) { st = ORC_E_RANGE; break; }
                     Pd[w] = (uint8_t)(delta + 1);
+                    Pp[w] = u;
                     Q0[tail++] = w;
                 }
                 if (st) break;
@@ -375,6 +399,7 @@ orc_index *orc_build_ex(uint32_t n, const uint32_t *off, const uint32_t *col,
         (void)visited;
         free(T);
         free(Pd);
+        free(Pp);
     }
 done:
     free(P); free(Sm1); free(S0); free(Q0); free(Q1); free(E0); free(E1);
@@ -449,6 +474,118 @@ void orc_export_bp_roots(const orc_index *ix, uint32_t *roots, uint32_t *cnt, ui
     memcpy(roots, ix->bp_root, (size_t)ix->t * sizeof(uint32_t));
     memcpy(cnt, ix->bp_cnt, (size_t)ix->t * sizeof(uint32_t));
     memcpy(S, ix->bp_S, (size_t)ix->t * BPW * sizeof(uint32_t));
+}
+
+/* parents[] in the layout of orc_export_labels, vertex ids (Sec. 6) */
+void orc_export_parents(const orc_index *ix, uint32_t *parents) {
+    uint64_t p = 0;
+    for (uint32_t v = 0; v < ix->n; ++v) {
+        memcpy(parents + p, ix->par[v], (size_t)ix->len[v] * sizeof(uint32_t));
+        p += ix->len[v];
+    }
+}
+
+/* ------------------------------------- Sec. 6: shortest-path queries */
+/* Exact distance from the bit-parallel vertex x of slot i to v, from the
+ * label of v: x = r_i when j < 0, else the j-th member of S_{r_i}, which lies
+ * at d(r_i, v) - 1, d(r_i, v) or d(r_i, v) + 1 from v as bit j is in
+ * S^{-1}_{r_i}(v), in S^0_{r_i}(v) or in neither (Sec. 5.1). -1: unreachable. */
+static int bp_dist_to(const orc_index *ix, uint32_t i, int j, uint32_t v) {
+    size_t k = (size_t)v * ix->t + i;
+    if (ix->bp_d[k] == INF8) return -1;
+    int d = ix->bp_d[k];
+    if (j < 0) return d;
+    uint64_t b = 1ull << j;
+    if (ix->bp_m1[k] & b) return d - 1;
+    if (ix->bp_m0[k] & b) return d;
+    return d + 1;
+}
+
+/* Walks from v to the bit-parallel vertex (i, j), each step to the first
+ * neighbour (in the graph's neighbour order) one hop nearer, writing v and
+ * every vertex after it at out[pos], out[pos + step], ... Returns 0, or -1 if
+ * some vertex has no nearer neighbour (impossible for a correct label). */
+static int bp_descend(const orc_index *ix, const uint32_t *off, const uint32_t *col, uint32_t i,
+                      int j, uint32_t v, uint32_t *out, long pos, long step) {
+    int dv = bp_dist_to(ix, i, j, v);
+    if (dv < 0) return -1;
+    out[pos] = v;
+    while (dv > 0) {
+        uint32_t next = NONE;
+        for (uint32_t e = off[v]; e < off[v + 1]; ++e)
+            if (bp_dist_to(ix, i, j, col[e]) == dv - 1) { next = col[e]; break; }
+        if (next == NONE) return -1;
+        v = next;
+        --dv;
+        pos += step;
+        out[pos] = v;
+    }
+    return 0;
+}
+
+/* Climbs the pruned BFS tree of hub rank h from v, which holds (h, d) in its
+ * label, up to the hub through the stored parents (Sec. 6), writing the d + 1
+ * vertices at out[pos], out[pos + step], ... Returns 0, or -1 if a parent does
+ * not hold (h, d - 1) (impossible for a correct index). */
+static int climb(const orc_index *ix, uint32_t h, uint32_t v, int d, uint32_t *out, long pos,
+                 long step) {
+    for (int k = d;; --k) {
+        out[pos] = v;
+        long x = -1;
+        for (uint32_t y = 0; y < ix->len[v]; ++y)
+            if (ix->hub[v][y] == h) { x = y; break; }
+        if (x < 0 || ix->dist[v][x] != k) return -1;
+        if (k == 0) return 0;
+        v = ix->par[v][x];
+        pos += step;
+    }
+}
+
+/* One shortest s-u path into out[0..d] (d = d_G(s, u), at most 255 vertices):
+ * returns the number of vertices, 0 if u is unreachable from s, or minus a
+ * status (ORC_E_INVAL for a bad id or a label that cannot be climbed,
+ * ORC_E_RANGE as for orc_query). The hub is the lowest-rank common hub of
+ * L(s) and L(u) whose distances add up to d; if there is none, the first
+ * bit-parallel slot i that reaches d gives the meeting vertex: a member of
+ * S_{r_i} in S^{-1} of both ends (d~ - 2), in S^{-1} of one and S^0 of the
+ * other (d~ - 1), or r_i itself (d~), lowest bit first. */
+long orc_path(const orc_index *ix, const uint32_t *off, const uint32_t *col, uint32_t s,
+              uint32_t u, uint32_t *out) {
+    if (s >= ix->n || u >= ix->n) return -ORC_E_INVAL;
+    int d = orc_query(ix, s, u);
+    if (d < 0) return d;
+    if (d == INF8) return 0;
+    if (s == u) { out[0] = s; return 1; }
+    uint32_t i = 0, j = 0;
+    while (i < ix->len[s] && j < ix->len[u]) {
+        uint32_t hs = ix->hub[s][i], hu = ix->hub[u][j];
+        if (hs == hu) {
+            int ds = ix->dist[s][i], du = ix->dist[u][j];
+            if (ds + du == d) {
+                if (climb(ix, hs, s, ds, out, 0, 1) || climb(ix, hs, u, du, out, d, -1))
+                    return -ORC_E_INVAL;
+                return d + 1;
+            }
+            ++i; ++j;
+        } else if (hs < hu) ++i;
+        else ++j;
+    }
+    for (uint32_t b = 0; b < ix->t; ++b) {
+        size_t ks = (size_t)s * ix->t + b, ku = (size_t)u * ix->t + b;
+        if (ix->bp_d[ks] == INF8 || ix->bp_d[ku] == INF8) continue;
+        int td = ix->bp_d[ks] + ix->bp_d[ku], x = -2;
+        uint64_t c;
+        if (td - 2 == d && (c = ix->bp_m1[ks] & ix->bp_m1[ku])) x = __builtin_ctzll(c);
+        else if (td - 1 == d && (c = (ix->bp_m1[ks] & ix->bp_m0[ku]) | (ix->bp_m0[ks] & ix->bp_m1[ku])))
+            x = __builtin_ctzll(c);
+        else if (td == d) x = -1;
+        if (x == -2) continue;
+        if (bp_dist_to(ix, b, x, s) + bp_dist_to(ix, b, x, u) != d) return -ORC_E_INVAL;
+        if (bp_descend(ix, off, col, b, x, s, out, 0, 1) || bp_descend(ix, off, col, b, x, u, out, d, -1))
+            return -ORC_E_INVAL;
+        return d + 1;
+    }
+    return -ORC_E_INVAL;
 }
 
 void orc_export_order(const orc_index *ix, uint32_t *order) {
