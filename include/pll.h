@@ -427,6 +427,66 @@ PLL_API int pll_learned_order(const uint32_t *offsets, const uint32_t *cols, uin
                               void *stream);
 
 /*
+ * Shortest-path queries (Sec. 6, "Shortest-Path Queries"): each label entry
+ * (h, d) of L(v) gets a parent, a neighbour of v whose label holds (h, d - 1),
+ * i.e. the next vertex towards h on a shortest path. A path is restored by
+ * climbing from s and from t towards the best common hub. Where only the
+ * bit-parallel label reaches d(s, t), the path runs through r_i or a member
+ * of S_{r_i}. The label gives that vertex's exact distance to every vertex
+ * (Sec. 5.1), so each end walks to it one hop at a time.
+ *
+ * pll_paths_create -- parents for every label entry of `idx`, plus a copy of
+ *   the graph in the index's rank space (4 (n + 1) + 4 nnz + 4 entries bytes
+ *   of device memory).
+ *     offsets, cols  device; the graph the index was built from (as for
+ *                    pll_build; the union CSR for pll_build_batch). Read only.
+ *     n, nnz         must equal the index's.
+ *     out            receives the object; free it with pll_paths_free.
+ *   The index is borrowed, not copied: it must outlive the object. A
+ *   malformed CSR, or a graph in which some label entry has no parent (not
+ *   the index's graph), gives PLL_E_INVAL. Synchronous. Errors: PLL_E_INVAL,
+ *   PLL_E_NOMEM, PLL_E_CUDA.
+ */
+typedef struct pll_paths pll_paths;
+PLL_API int pll_paths_create(const pll_index *idx, const uint32_t *offsets, const uint32_t *cols,
+                             uint32_t n, uint64_t nnz, void *stream, pll_paths **out);
+
+/* pll_paths_parents -- host parents[total entries] in the layout of
+ * pll_export_labels (vertices by caller id, hubs ascending): the caller id
+ * of the parent of v for that hub; v itself for the entry (v, 0).
+ * Synchronous. */
+PLL_API int pll_paths_parents(const pll_paths *p, uint32_t *parents);
+
+/* pll_path_offsets -- slot offsets for pll_path_query.
+ *   src, dst   device uint32[q], caller ids.
+ *   path_off   device uint64[q + 1]: path_off[i] = sum over j < i of the
+ *              vertex count of pair j's path (d(s_j, t_j) + 1, 0 when
+ *              unreachable); path_off[q] = the total.
+ *   total      host; receives path_off[q].
+ * q < 2^31 - 1 (else PLL_E_RANGE). Synchronous. Errors: PLL_E_INVAL (null
+ * pointer, id >= n), PLL_E_RANGE (a finite distance >= 255), PLL_E_CUDA. */
+PLL_API int pll_path_offsets(const pll_paths *p, const uint32_t *src, const uint32_t *dst,
+                             uint64_t q, uint64_t *path_off, uint64_t *total, void *stream);
+
+/* pll_path_query -- one shortest path per pair.
+ *   src, dst   device uint32[q], caller ids.
+ *   path_off   device uint64[q + 1]: pair i owns path[path_off[i],
+ *              path_off[i + 1]); e.g. the output of pll_path_offsets.
+ *   cap        elements of `path`; every path_off[i + 1] must be <= cap.
+ *   path       device uint32[cap], caller-owned. Pair i gets s_i, ..., t_i
+ *              (d + 1 caller ids; only s_i when s_i = t_i; none when t_i is
+ *              unreachable). The rest of its slot is set to 0xffffffff.
+ * Synchronous. Errors: PLL_E_INVAL (null pointer; offsets that decrease or
+ * pass cap, whose pair is left unwritten; an id >= n or a slot shorter than
+ * its path, whose slot is all 0xffffffff), PLL_E_RANGE (a finite distance
+ * >= 255), PLL_E_CUDA. */
+PLL_API int pll_path_query(const pll_paths *p, const uint32_t *src, const uint32_t *dst,
+                           uint64_t q, const uint64_t *path_off, uint64_t cap, uint32_t *path,
+                           void *stream);
+
+PLL_API void pll_paths_free(pll_paths *p);
+
+/*
  * The index as a file (the paper answers queries from a disk-resident index,
  * Sec. 6; here the file is an image to keep and load, not to query in place).
  *

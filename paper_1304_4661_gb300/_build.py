@@ -31,6 +31,7 @@ CU_SOURCES = [
     "pll_serve.cu",
     "k_learned.cu",
     "pll_io.cu",
+    "pll_paths.cu",
 ]
 
 

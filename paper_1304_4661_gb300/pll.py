@@ -31,6 +31,8 @@ SYMBOLS = [
     "pll_mlp_set_params", "pll_mlp_get_params", "pll_mlp_forward", "pll_mlp_grad",
     "pll_mlp_read_grad", "pll_mlp_adam", "pll_mlp_train_step", "pll_learned_order",
     "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs",
+    "pll_paths_create", "pll_paths_parents", "pll_path_offsets", "pll_path_query",
+    "pll_paths_free",
 ]
 MLP_NPARAM = 4801
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -161,6 +163,16 @@ def load(build_if_missing: bool = True):
     lib.pll_save.argtypes = [vp, C.c_char_p]
     lib.pll_load.restype = i32
     lib.pll_load.argtypes = [C.c_char_p, pp]
+    lib.pll_paths_create.restype = i32
+    lib.pll_paths_create.argtypes = [vp, vp, vp, u32, u64, vp, pp]
+    lib.pll_paths_parents.restype = i32
+    lib.pll_paths_parents.argtypes = [vp, vp]
+    lib.pll_path_offsets.restype = i32
+    lib.pll_path_offsets.argtypes = [vp, vp, vp, u64, vp, C.POINTER(C.c_uint64), vp]
+    lib.pll_path_query.restype = i32
+    lib.pll_path_query.argtypes = [vp, vp, vp, u64, vp, u64, vp, vp]
+    lib.pll_paths_free.restype = None
+    lib.pll_paths_free.argtypes = [vp]
     lib.pll_test_fail_alloc.restype = None
     lib.pll_test_fail_alloc.argtypes = [C.c_int64]
     lib.pll_test_live_allocs.restype = C.c_int64
@@ -404,6 +416,79 @@ class Index:
         s = Stats()
         _check(load().pll_get_stats(self._h, C.byref(s)), "pll_get_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class Paths:
+    """pll_paths_*: shortest-path queries (Sec. 6) over an Index built from
+    the graph given here (CUDA tensors, as for Index.build)."""
+
+    def __init__(self, index: "Index", offsets, cols, stream=None):
+        self._lib = load()
+        self.index = index  # the paths object borrows the index
+        n = int(offsets.shape[0]) - 1
+        nnz = int(cols.shape[0])
+        h = C.c_void_p()
+        _check(self._lib.pll_paths_create(index._h, _dptr(offsets), _dptr(cols) if nnz else None, n,
+                                          nnz, _stream_handle(stream), C.byref(h)), "pll_paths_create")
+        self._h = h.value
+
+    def parents(self) -> np.ndarray:
+        """Parent (caller id) of every label entry, in the layout of Index.labels()."""
+        tot = self.index.label_entries()
+        out = np.empty(max(tot, 1), dtype=np.uint32)
+        _check(self._lib.pll_paths_parents(self._h, out.ctypes.data), "pll_paths_parents")
+        return out[:tot]
+
+    def offsets(self, src, dst, stream=None):
+        """pll_path_offsets: (path_off int64 CUDA [q + 1], total)."""
+        import torch
+        q = int(src.shape[0])
+        off = torch.empty(q + 1, dtype=torch.int64, device=src.device)
+        tot = C.c_uint64(0)
+        _check(self._lib.pll_path_offsets(self._h, _dptr(src) if q else None, _dptr(dst) if q else None,
+                                          q, _dptr(off), C.byref(tot), _stream_handle(stream)),
+               "pll_path_offsets")
+        return off, int(tot.value)
+
+    def query(self, src, dst, path_off=None, cap=None, stream=None):
+        """pll_path_query on CUDA tensors: returns (path_off, path), pair i's
+        path (caller ids) in path[path_off[i]:path_off[i + 1]]. Without
+        path_off the slots come from offsets()."""
+        import torch
+        q = int(src.shape[0])
+        if path_off is None:
+            path_off, cap = self.offsets(src, dst, stream)
+        elif cap is None:
+            cap = int(path_off[-1].item()) if q else 0
+        path = torch.empty(max(cap, 1), dtype=torch.int32, device=src.device)
+        if q:
+            _check(self._lib.pll_path_query(self._h, _dptr(src), _dptr(dst), q, _dptr(path_off), cap,
+                                            _dptr(path), _stream_handle(stream)), "pll_path_query")
+        return path_off, path[:cap]
+
+    def paths(self, src, dst, stream=None):
+        """Host list of numpy uint32 paths, one per pair."""
+        off, path = self.query(src, dst, stream=stream)
+        off = off.cpu().numpy()
+        p = path.cpu().numpy().view(np.uint32)
+        return [p[off[i]:off[i + 1]] for i in range(len(off) - 1)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pll_paths_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -25,45 +25,10 @@ import oracle
 from paper_1304_4661_gb300 import graphgen as gg
 
 from . import brute, graphs
+from .paths_util import adjacency_sets, check_parents, check_path
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 INF = 255
-
-
-def adjacency_sets(g):
-    off = g.offsets.astype(np.int64)
-    return [set(g.cols[off[v]:off[v + 1]].tolist()) for v in range(g.n)]
-
-
-def check_path(p, s, u, D, adj):
-    d = int(D[s, u])
-    if d >= INF:
-        assert len(p) == 0, (s, u, p)
-        return
-    assert len(p) == d + 1, (s, u, d, p)
-    assert p[0] == s and p[-1] == u, (s, u, p)
-    for a, b in zip(p[:-1], p[1:]):
-        assert b in adj[a], (s, u, p)
-
-
-def check_parents(g, ix, D):
-    L, P = ix.labels(), ix.parents()
-    order = ix.order()
-    adj = adjacency_sets(g)
-    where = {}
-    for v in range(g.n):
-        for x in range(int(L.offsets[v]), int(L.offsets[v + 1])):
-            where[(v, int(L.hubs[x]))] = int(L.dists[x])
-    for v in range(g.n):
-        for x in range(int(L.offsets[v]), int(L.offsets[v + 1])):
-            h, d, p = int(L.hubs[x]), int(L.dists[x]), int(P[x])
-            hv = int(order[h])
-            if d == 0:
-                assert p == v == hv, (v, h, p)
-                continue
-            assert p in adj[v], (v, h, p)
-            assert D[hv, p] == d - 1, (v, h, p)
-            assert where.get((p, h)) == d - 1, (v, h, p)
 
 
 def test_hand_worked_parents_and_paths():
@@ -85,7 +50,7 @@ def test_hand_worked_parents_and_paths():
 def test_parents_and_every_path(g, t):
     D = brute.apsp(g.offsets, g.cols)
     ix = oracle.Index(g.offsets, g.cols, t)
-    check_parents(g, ix, D)
+    check_parents(g, ix.labels(), ix.parents(), ix.order(), D)
     adj = adjacency_sets(g)
     for s in range(g.n):
         for u in range(g.n):
@@ -132,7 +97,7 @@ def test_trees_parents_and_paths_are_unique(n, seed, t):
 def test_sampled_paths_larger_graphs(g, t):
     D = brute.apsp(g.offsets, g.cols)
     ix = oracle.Index(g.offsets, g.cols, t)
-    check_parents(g, ix, D)
+    check_parents(g, ix.labels(), ix.parents(), ix.order(), D)
     adj = adjacency_sets(g)
     s, u = gg.pairs(g.n, 3000, 9)
     for a, b in zip(s.tolist(), u.tolist()):
