@@ -777,6 +777,75 @@ def run_variants(args, ws, rank, local):
         print(json.dumps(outj), flush=True)
 
 
+def run_paths(args, ws, rank, local):
+    """Shortest-path queries (Sec. 6) over the R-MAT-20 index (t = 64): the
+    parent pass (pll_paths_create) once, then per step 1M uniform pairs through
+    pll_path_offsets + pll_path_query, beside the distance-only query of the
+    same pairs. The index (1.4 GB) and the paths (tens of MB) are larger than
+    L2."""
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    g = gg.rmat(20, 16, seed=1)
+    d_off, d_col = dev(g.offsets), dev(g.cols)
+    ix = pll.Index.build(d_off, d_col, t=64)
+    pms, P = timed(lambda: pll.Paths(ix, d_off, d_col))
+    q = 1_000_000
+    s, u = gg.pairs(g.n, q, 3)
+    ds, du = dev(s), dev(u)
+    out = torch.empty(q, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        P.query(ds, du)
+        ix.query_async(ds, du, out)
+    pt, qt = [], []
+    verts = 0
+    barrier(ws)
+    for _ in range(args.steps):
+        ms, (off, path) = timed(lambda: P.query(ds, du))
+        pt.append(ms)
+        verts = int(path.numel())
+        qt.append(timed(lambda: ix.query_async(ds, du, out))[0])
+    barrier(ws)
+    mean_ms = max_over_ranks(ws, statistics.mean(pt))
+    reach = int((out != 255).sum().item())
+    outj = {"metric": "Shortest-path queries (Sec. 6) on R-MAT-20, t = 64: paths per second",
+            "value": round(job_rate(ws, q * args.steps, mean_ms * 1e-3 * args.steps), 1),
+            "unit": "paths/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(mean_ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "R-MAT-20 (seed 1, ef 16), t = 64, 1M uniform pairs (seed 3); "
+                                   "inputs larger than L2 (index 1.4 GB)"},
+            "parents_ms": round(pms, 2), "label_entries": ix.label_entries(),
+            "reachable_pairs": reach, "path_vertices_per_step": verts,
+            "path_vertices_per_s": round(verts / (mean_ms * 1e-3), 1),
+            "distance_query_ms": round(statistics.mean(qt), 3),
+            "gpu_launches": 3 * args.steps}
+    P.close()
+    ix.close()
+    if rank == 0:
+        print(json.dumps(outj), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_baseline(args, scale=None):
     """The oracle as it stands (single thread) on a bounded sample: a full
@@ -840,7 +909,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned", "variants"], default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned", "variants", "paths"], default="rmat20")
     ap.add_argument("--root-batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--latency-samples", type=int, default=2000)
@@ -858,10 +927,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload in ("batch256", "serve", "learned", "variants"):
+    if args.workload in ("batch256", "serve", "learned", "variants", "paths"):
         ws, rank, local = dist_setup()
         {"batch256": run_batch, "serve": run_serve, "learned": run_learned,
-         "variants": run_variants}[args.workload](args, ws, rank, local)
+         "variants": run_variants, "paths": run_paths}[args.workload](args, ws, rank, local)
         return
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup() if args.impl == "ours" else (
