@@ -9,8 +9,9 @@ imports the product: the two meet only through the seeded inputs.
 the Degree order (Sec. 4.4.2), bit-parallel labels (Alg. 3, Sec. 5),
 the pruned BFSs of Alg. 1/2 with bit-parallel pruning (Sec. 5.4), the
 label query (Sec. 3.3, Sec. 5.3), plain BFS, the closed form of one
-label derived from Thm 4.1 / Thm 4.2, and the parents and path restoration
-of the shortest-path queries of Sec. 6 (see the header of oracle.c).
+label derived from Thm 4.1 / Thm 4.2, the parents and path restoration of
+the shortest-path queries of Sec. 6, and the directed-graph labels of Sec. 6
+(see the header of oracle.c).
 """
 from __future__ import annotations
 
@@ -77,6 +78,20 @@ def _load():
         lib.orc_export_parents.argtypes = [vp, vp]
         lib.orc_path.restype = C.c_long
         lib.orc_path.argtypes = [vp, vp, vp, u32, u32, vp]
+        lib.orc_build_directed.restype = vp
+        lib.orc_build_directed.argtypes = [u32, vp, vp, vp, C.POINTER(C.c_int)]
+        lib.orc_dfree.restype = None
+        lib.orc_dfree.argtypes = [vp]
+        lib.orc_dquery.restype = i32
+        lib.orc_dquery.argtypes = [vp, u32, u32]
+        lib.orc_dquery_batch.restype = i32
+        lib.orc_dquery_batch.argtypes = [vp, u64, vp, vp, vp]
+        lib.orc_dtotal.restype = u64
+        lib.orc_dtotal.argtypes = [vp, i32]
+        lib.orc_dexport.restype = None
+        lib.orc_dexport.argtypes = [vp, i32, vp, vp, vp]
+        lib.orc_dexport_order.restype = None
+        lib.orc_dexport_order.argtypes = [vp, vp]
         lib.orc_export_order.restype = None
         lib.orc_export_order.argtypes = [vp, vp]
         lib.orc_counters.restype = None
@@ -239,6 +254,68 @@ class Index:
         _load().orc_counters(self._h, out.ctypes.data)
         return dict(visited=int(out[0]), labeled=int(out[1]), scanned=int(out[2]),
                     labeled_deg=int(out[3]))
+
+
+class DirectedIndex:
+    """Directed-graph index of Sec. 6: L_IN and L_OUT from a forward and a
+    reverse pruned BFS per root, no bit-parallel labels. offsets/cols list
+    the out-arcs of each vertex."""
+
+    def __init__(self, offsets, cols, order=None):
+        self._off, self._col = _u32(offsets), _u32(cols)
+        self.n = self._off.shape[0] - 1
+        lib = _load()
+        st = C.c_int(0)
+        ordp = None
+        if order is not None:
+            self._ord = _u32(order)
+            ordp = self._ord.ctypes.data
+        self._h = lib.orc_build_directed(self.n, self._off.ctypes.data, self._col.ctypes.data, ordp,
+                                         C.byref(st))
+        if not self._h:
+            raise OracleError(st.value, "build_directed")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _load().orc_dfree(h)
+            self._h = None
+
+    def query(self, s: int, t: int) -> int:
+        d = _load().orc_dquery(self._h, s, t)
+        if d < 0:
+            raise OracleError(-d, "dquery")
+        return d
+
+    def query_batch(self, s, t) -> np.ndarray:
+        s, t = _u32(s), _u32(t)
+        out = np.empty(max(s.shape[0], 1), dtype=np.uint8)
+        st = _load().orc_dquery_batch(self._h, s.shape[0], s.ctypes.data, t.ctypes.data, out.ctypes.data)
+        if st:
+            raise OracleError(st, "dquery_batch")
+        return out[: s.shape[0]]
+
+    def _labels(self, which: int) -> Labels:
+        lib = _load()
+        tot = lib.orc_dtotal(self._h, which)
+        off = np.empty(self.n + 1, dtype=np.uint64)
+        hubs = np.empty(max(tot, 1), dtype=np.uint32)
+        dists = np.empty(max(tot, 1), dtype=np.uint8)
+        lib.orc_dexport(self._h, which, off.ctypes.data, hubs.ctypes.data, dists.ctypes.data)
+        return Labels(off, hubs[:tot], dists[:tot])
+
+    def labels_in(self) -> Labels:
+        """L_IN(v): (hub rank, d(hub, v))."""
+        return self._labels(0)
+
+    def labels_out(self) -> Labels:
+        """L_OUT(v): (hub rank, d(v, hub))."""
+        return self._labels(1)
+
+    def order(self) -> np.ndarray:
+        out = np.empty(max(self.n, 1), dtype=np.uint32)
+        _load().orc_dexport_order(self._h, out.ctypes.data)
+        return out[: self.n]
 
 
 def label_of(offsets, cols, rank, inX, u: int):

@@ -43,6 +43,10 @@
  *                         gives exactly (Sec. 5.1); each step moves to the
  *                         first neighbour one hop nearer.
  *
+ *   orc_build_directed -- Sec. 6, "Directed Graphs": labels L_IN and L_OUT
+ *                         from a forward and a reverse pruned BFS per root;
+ *   orc_dquery         -- d(s, t) from L_OUT(s) and L_IN(t).
+ *
  *   orc_core_numbers   -- core number of every vertex (the largest k such that
  *                         the vertex lies in a subgraph of minimum degree k),
  *                         one of the vertex features of the learned order; the
@@ -712,4 +716,217 @@ int orc_core_numbers(uint32_t n, const uint32_t *off, const uint32_t *col, uint3
     memcpy(core, deg, sizeof(uint32_t) * n);
     free(deg); free(pos); free(vert); free(bin);
     return ORC_OK;
+}
+
+/* ------------------------------------------------ Sec. 6: directed graphs */
+/* Two label sets per vertex (Sec. 6, "Directed Graphs"): L_IN(v) holds
+ * (u, d(u, v)) and L_OUT(v) holds (u, d(v, u)), hubs as ranks. Each root v_k,
+ * in rank order, runs a pruned BFS forward along arcs, which fills L_IN and
+ * prunes u when L_OUT(v_k) and L_IN(u) already give d(v_k, u), and one in
+ * reverse, which fills L_OUT and prunes u when L_OUT(u) and L_IN(v_k) already
+ * give d(u, v_k). Readings: the Degree order counts in- plus out-arcs (ties by
+ * ascending id); the forward pass runs first (the order of the two passes
+ * does not change the labels: a root's own hub enters neither prune test);
+ * there are no bit-parallel labels (Sec. 5's masks need |d(s, v) - d(r, v)|
+ * <= 1 for neighbours s of r, which arcs one way do not give). */
+typedef struct orc_label_set {
+    uint32_t *len, *cap;
+    uint32_t **hub;
+    uint8_t **dist;
+} orc_label_set;
+
+typedef struct orc_dindex {
+    uint32_t n;
+    uint32_t *order, *rank;
+    orc_label_set in, out;
+} orc_dindex;
+
+static int set_alloc(orc_label_set *L, uint32_t n) {
+    L->len = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
+    L->cap = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
+    L->hub = (uint32_t **)calloc((size_t)n + 1, sizeof(uint32_t *));
+    L->dist = (uint8_t **)calloc((size_t)n + 1, sizeof(uint8_t *));
+    return (L->len && L->cap && L->hub && L->dist) ? ORC_OK : ORC_E_NOMEM;
+}
+
+static void set_free(orc_label_set *L, uint32_t n) {
+    if (L->hub) for (uint32_t v = 0; v < n; ++v) free(L->hub[v]);
+    if (L->dist) for (uint32_t v = 0; v < n; ++v) free(L->dist[v]);
+    free(L->len); free(L->cap); free(L->hub); free(L->dist);
+}
+
+static int set_push(orc_label_set *L, uint32_t u, uint32_t hub, uint8_t d) {
+    if (L->len[u] == L->cap[u]) {
+        uint32_t nc = L->cap[u] ? 2 * L->cap[u] : 4;
+        uint32_t *h = (uint32_t *)realloc(L->hub[u], (size_t)nc * sizeof(uint32_t));
+        if (!h) return ORC_E_NOMEM;
+        L->hub[u] = h;
+        uint8_t *dd = (uint8_t *)realloc(L->dist[u], nc);
+        if (!dd) return ORC_E_NOMEM;
+        L->dist[u] = dd;
+        L->cap[u] = nc;
+    }
+    L->hub[u][L->len[u]] = hub;
+    L->dist[u][L->len[u]] = d;
+    L->len[u]++;
+    return ORC_OK;
+}
+
+void orc_dfree(orc_dindex *ix) {
+    if (!ix) return;
+    set_free(&ix->in, ix->n);
+    set_free(&ix->out, ix->n);
+    free(ix->order); free(ix->rank);
+    free(ix);
+}
+
+/* Alg. 1 for root v_k in one direction: follow the arcs of (off, col); the
+ * root's own labels `from` give T, the visited vertices are tested against and
+ * labelled in `to`. */
+static int pruned_bfs_dir(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t k,
+                          uint32_t vk, const orc_label_set *from, orc_label_set *to, uint8_t *T,
+                          uint8_t *Pd, uint32_t *Q) {
+    (void)n;
+    int st = ORC_OK;
+    for (uint32_t x = 0; x < from->len[vk]; ++x) T[from->hub[vk][x]] = from->dist[vk][x];
+    uint32_t head = 0, tail = 0;
+    Q[tail++] = vk;
+    Pd[vk] = 0;
+    while (head < tail && st == ORC_OK) {
+        uint32_t u = Q[head++];
+        int delta = Pd[u], pruned = 0;
+        for (uint32_t x = 0; x < to->len[u]; ++x) {
+            uint8_t tw = T[to->hub[u][x]];
+            if (tw != INF8 && (int)tw + to->dist[u][x] <= delta) { pruned = 1; break; }
+        }
+        if (pruned) continue;
+        if ((st = set_push(to, u, k, (uint8_t)delta))) break;
+        for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+            uint32_t w = col[e];
+            if (Pd[w] != INF8) continue;
+            if (delta + 1 >= INF8) { st = ORC_E_RANGE; break; }
+            Pd[w] = (uint8_t)(delta + 1);
+            Q[tail++] = w;
+        }
+    }
+    for (uint32_t x = 0; x < tail; ++x) Pd[Q[x]] = INF8;
+    for (uint32_t x = 0; x < from->len[vk]; ++x) T[from->hub[vk][x]] = INF8;
+    return st;
+}
+
+/* off, col: arcs u -> col[e] for e in [off[u], off[u+1]) (out-neighbours;
+ * self-loops and repeated arcs are allowed and change nothing). order: rank
+ * -> vertex, or NULL for the Degree order by in- plus out-degree. */
+orc_dindex *orc_build_directed(uint32_t n, const uint32_t *off, const uint32_t *col,
+                               const uint32_t *order, int *status) {
+    int st = ORC_OK;
+    orc_dindex *ix = (orc_dindex *)calloc(1, sizeof(orc_dindex));
+    if (!ix) { *status = ORC_E_NOMEM; return NULL; }
+    ix->n = n;
+    uint64_t m = off[n];
+    ix->order = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    ix->rank = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    uint32_t *roff = (uint32_t *)calloc((size_t)n + 2, sizeof(uint32_t));
+    uint32_t *rcol = (uint32_t *)malloc((m + 1) * sizeof(uint32_t));
+    uint32_t *deg = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
+    uint8_t *T = (uint8_t *)malloc((size_t)n + 1), *Pd = (uint8_t *)malloc((size_t)n + 1);
+    uint32_t *Q = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    if (!ix->order || !ix->rank || !roff || !rcol || !deg || !T || !Pd || !Q ||
+        set_alloc(&ix->in, n) || set_alloc(&ix->out, n)) { st = ORC_E_NOMEM; goto done; }
+    for (uint64_t e = 0; e < m; ++e)
+        if (col[e] >= n) { st = ORC_E_INVAL; goto done; }
+    /* reverse arcs: in-neighbours of each vertex */
+    for (uint64_t e = 0; e < m; ++e) roff[col[e] + 1]++;
+    for (uint32_t v = 0; v < n; ++v) roff[v + 1] += roff[v];
+    {
+        uint32_t *fill = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+        if (!fill) { st = ORC_E_NOMEM; goto done; }
+        memcpy(fill, roff, (size_t)n * sizeof(uint32_t));
+        for (uint32_t u = 0; u < n; ++u)
+            for (uint32_t e = off[u]; e < off[u + 1]; ++e) rcol[fill[col[e]]++] = u;
+        free(fill);
+    }
+    if (order) {
+        for (uint32_t v = 0; v < n; ++v) ix->rank[v] = NONE;
+        for (uint32_t k = 0; k < n; ++k) {
+            if (order[k] >= n || ix->rank[order[k]] != NONE) { st = ORC_E_ORDER; goto done; }
+            ix->order[k] = order[k];
+            ix->rank[order[k]] = k;
+        }
+    } else {
+        for (uint32_t v = 0; v < n; ++v) {
+            deg[v] = (off[v + 1] - off[v]) + (roff[v + 1] - roff[v]);
+            ix->order[v] = v;
+        }
+        g_deg_for_sort = deg;
+        qsort(ix->order, n, sizeof(uint32_t), cmp_degree);
+        for (uint32_t k = 0; k < n; ++k) ix->rank[ix->order[k]] = k;
+    }
+    memset(T, INF8, n);
+    memset(Pd, INF8, n);
+    for (uint32_t k = 0; k < n && st == ORC_OK; ++k) {
+        uint32_t vk = ix->order[k];
+        st = pruned_bfs_dir(n, off, col, k, vk, &ix->out, &ix->in, T, Pd, Q);
+        if (st == ORC_OK) st = pruned_bfs_dir(n, roff, rcol, k, vk, &ix->in, &ix->out, T, Pd, Q);
+    }
+done:
+    free(roff); free(rcol); free(deg); free(T); free(Pd); free(Q);
+    if (st) { orc_dfree(ix); *status = st; return NULL; }
+    *status = ORC_OK;
+    return ix;
+}
+
+/* d(s, t) from L_OUT(s) and L_IN(t) (merge join over hub ranks); 255 if they
+ * share no hub; -ORC_E_RANGE if the minimum is finite but >= 255. */
+int orc_dquery(const orc_dindex *ix, uint32_t s, uint32_t t) {
+    const orc_label_set *A = &ix->out, *B = &ix->in;
+    int best = 1 << 20;
+    uint32_t i = 0, j = 0;
+    while (i < A->len[s] && j < B->len[t]) {
+        uint32_t hs = A->hub[s][i], ht = B->hub[t][j];
+        if (hs == ht) {
+            int d = A->dist[s][i] + B->dist[t][j];
+            if (d < best) best = d;
+            ++i; ++j;
+        } else if (hs < ht) ++i;
+        else ++j;
+    }
+    if (best >= (1 << 20)) return INF8;
+    if (best >= INF8) return -ORC_E_RANGE;
+    return best;
+}
+
+int orc_dquery_batch(const orc_dindex *ix, uint64_t q, const uint32_t *s, const uint32_t *t,
+                     uint8_t *out) {
+    int st = ORC_OK;
+    for (uint64_t x = 0; x < q; ++x) {
+        if (s[x] >= ix->n || t[x] >= ix->n) return ORC_E_INVAL;
+        int d = orc_dquery(ix, s[x], t[x]);
+        if (d < 0) { st = -d; out[x] = INF8; } else out[x] = (uint8_t)d;
+    }
+    return st;
+}
+
+/* which = 0: L_IN, 1: L_OUT */
+uint64_t orc_dtotal(const orc_dindex *ix, int which) {
+    const orc_label_set *L = which ? &ix->out : &ix->in;
+    uint64_t s = 0;
+    for (uint32_t v = 0; v < ix->n; ++v) s += L->len[v];
+    return s;
+}
+
+void orc_dexport(const orc_dindex *ix, int which, uint64_t *offsets, uint32_t *hubs, uint8_t *dists) {
+    const orc_label_set *L = which ? &ix->out : &ix->in;
+    uint64_t p = 0;
+    for (uint32_t v = 0; v < ix->n; ++v) {
+        offsets[v] = p;
+        memcpy(hubs + p, L->hub[v], (size_t)L->len[v] * sizeof(uint32_t));
+        memcpy(dists + p, L->dist[v], L->len[v]);
+        p += L->len[v];
+    }
+    offsets[ix->n] = p;
+}
+
+void orc_dexport_order(const orc_dindex *ix, uint32_t *order) {
+    memcpy(order, ix->order, (size_t)ix->n * sizeof(uint32_t));
 }

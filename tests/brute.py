@@ -17,6 +17,12 @@ library all-pairs BFS (scipy.sparse.csgraph), so it can pin the oracle:
                          to -1 and 0.
 * ``label_query``     -- Query(s, t, L) of Sec. 3.3 written as a set
                          intersection (no merge).
+* ``apsp_directed``, ``canonical_directed`` -- the same for the directed
+                         labels of Sec. 6: (v_j, d(v_j, u)) is in L_IN(u)
+                         iff no v_i with i < j lies on a shortest v_j -> u
+                         path, and (v_j, d(u, v_j)) is in L_OUT(u) iff none
+                         lies on a shortest u -> v_j path (the arguments of
+                         Thm 4.1 and Thm 4.2 run unchanged along arcs).
 """
 from __future__ import annotations
 
@@ -97,3 +103,44 @@ def label_query(La, Lb) -> int:
         if h in da:
             best = min(best, da[h] + x)
     return best
+
+
+def apsp_directed(offsets, cols) -> np.ndarray:
+    """d(u, v) along arcs (out-neighbour CSR), 255 = unreachable."""
+    n = len(offsets) - 1
+    if n == 0:
+        return np.zeros((0, 0), dtype=np.int64)
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(offsets, dtype=np.int64)))
+    A = sp.csr_matrix((np.ones(len(cols)), (rows, np.asarray(cols, dtype=np.int64))), shape=(n, n))
+    D = shortest_path(A, method="D", unweighted=True, directed=True)
+    out = np.full((n, n), INF, dtype=np.int64)
+    fin = np.isfinite(D)
+    out[fin] = D[fin].astype(np.int64)
+    return out
+
+
+def canonical_directed(D: np.ndarray, order):
+    """({u: [(rank j, d)]} for L_IN, the same for L_OUT), hubs ascending."""
+    n = D.shape[0]
+    order = np.asarray(order, dtype=np.int64)
+    rank = np.empty(n, dtype=np.int64)
+    rank[order] = np.arange(n)
+    Dw = np.where(D >= INF, 10**6, D)
+    Lin = {u: [] for u in range(n)}
+    Lout = {u: [] for u in range(n)}
+    for j in range(n):
+        v = order[j]
+        early = rank < j
+        # forward: w on a shortest v -> u path iff d(v, w) + d(w, u) = d(v, u)
+        on_fwd = (Dw[v][:, None] + Dw) == Dw[v][None, :]
+        blocked_in = (on_fwd & early[:, None]).any(axis=0)
+        # reverse: w on a shortest u -> v path iff d(u, w) + d(w, v) = d(u, v)
+        on_rev = (Dw + Dw[:, v][None, :]) == Dw[:, v][:, None]
+        blocked_out = (on_rev & early[None, :]).any(axis=1)
+        for u in range(n):
+            if D[v, u] < INF and not blocked_in[u]:
+                Lin[u].append((j, int(D[v, u])))
+            if D[u, v] < INF and not blocked_out[u]:
+                Lout[u].append((j, int(D[u, v])))
+    return Lin, Lout
+
