@@ -227,3 +227,54 @@ def learned_training_specs(count: int = 200, seed: int = 11, scales=(14, 15, 16)
     u = uniform(seed, count)
     k = len(scales)
     return [(scales[min(k - 1, int(u[i] * k))], first_seed + i) for i in range(count)]
+
+
+# ------------------------------------------------------------ directed graphs
+@dataclass
+class Digraph:
+    """Directed graph as an out-neighbour CSR: arcs u -> cols[e] for e in
+    [offsets[u], offsets[u + 1]), ascending, no repeats, no self-loops."""
+
+    n: int
+    offsets: np.ndarray  # uint32 [n + 1]
+    cols: np.ndarray     # uint32 [nnz]
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.cols.shape[0])
+
+
+def digraph(n: int, arcs, name: str = "arcs") -> Digraph:
+    """Digraph from (u, v) arcs; self-loops and repeats are dropped."""
+    a = np.asarray(list(arcs), dtype=np.int64).reshape(-1, 2)
+    a = a[a[:, 0] != a[:, 1]]
+    if a.shape[0]:
+        a = np.unique(a, axis=0)  # sorted by (u, v)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, a[:, 0] + 1, 1)
+    return Digraph(n, np.cumsum(off).astype(np.uint32), a[:, 1].astype(np.uint32), name)
+
+
+def random_digraph(n: int, m: int, seed: int) -> Digraph:
+    """m arcs with both ends uniform on [0, n) (repeats and self-loops then
+    dropped)."""
+    if n == 0 or m == 0:
+        return digraph(n, [], f"rand_digraph(n={n},m={m},seed={seed})")
+    x = below(seed, 2 * m, n).astype(np.int64).reshape(m, 2)
+    return digraph(n, x, f"rand_digraph(n={n},m={m},seed={seed})")
+
+
+def oriented(g: Graph, seed: int, both: float = 0.3) -> Digraph:
+    """A digraph from an undirected graph: each edge {u, v} becomes both arcs
+    with probability `both`, else one arc in a uniformly chosen direction."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets.astype(np.int64)))
+    cols = g.cols.astype(np.int64)
+    keep = rows < cols
+    u, v = rows[keep], cols[keep]
+    r = uniform(seed, 2 * len(u)).reshape(-1, 2) if len(u) else np.zeros((0, 2))
+    two = r[:, 0] < both
+    fwd = r[:, 1] < 0.5
+    arcs = np.concatenate([np.stack([u[two | fwd], v[two | fwd]], 1),
+                           np.stack([v[two | ~fwd], u[two | ~fwd]], 1)])
+    return digraph(g.n, arcs, f"oriented({g.name},seed={seed},both={both})")

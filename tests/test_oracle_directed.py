@@ -27,38 +27,19 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 INF = 255
 
 
-def digraph(n, arcs):
-    """Out-neighbour CSR (ascending, no repeats) from an arc list."""
-    arcs = sorted(set((int(a), int(b)) for a, b in arcs))
-    off = np.zeros(n + 1, dtype=np.uint32)
-    for a, _ in arcs:
-        off[a + 1] += 1
-    off = np.cumsum(off).astype(np.uint32)
-    col = np.array([b for _, b in arcs], dtype=np.uint32)
-    return off, col
-
-
-def random_digraph(n, p, seed, loops=False):
-    rng = np.random.default_rng(seed)
-    A = rng.random((n, n)) < p
-    if not loops:
-        np.fill_diagonal(A, False)
-    a, b = np.nonzero(A)
-    return digraph(n, zip(a.tolist(), b.tolist()))
-
-
 def family():
-    out = [("dcycle9", digraph(9, [(i, (i + 1) % 9) for i in range(9)])),
-           ("dpath12", digraph(12, [(i, i + 1) for i in range(11)])),
-           ("dag", digraph(10, [(i, j) for i in range(10) for j in range(i + 1, 10) if (i * 7 + j) % 3 == 0])),
-           ("out_star", digraph(8, [(0, i) for i in range(1, 8)])),
-           ("in_star", digraph(8, [(i, 0) for i in range(1, 8)])),
-           ("empty6", digraph(6, [])),
-           ("single", digraph(1, []))]
-    for n, p, sd in ((20, 0.08, 1), (30, 0.05, 2), (40, 0.1, 3), (60, 0.03, 4), (80, 0.04, 5)):
-        out.append((f"rand{n}_{sd}", random_digraph(n, p, sd)))
-    out.append(("loops25", random_digraph(25, 0.1, 6, loops=True)))
-    return out
+    """(name, offsets, cols) of small digraphs: cycle, path, DAG, stars,
+    empty, single vertex, uniform random arcs, oriented power-law graphs."""
+    gs = [gg.digraph(9, [(i, (i + 1) % 9) for i in range(9)], "dcycle9"),
+          gg.digraph(12, [(i, i + 1) for i in range(11)], "dpath12"),
+          gg.digraph(10, [(i, j) for i in range(10) for j in range(i + 1, 10) if (i * 7 + j) % 3 == 0], "dag"),
+          gg.digraph(8, [(0, i) for i in range(1, 8)], "out_star"),
+          gg.digraph(8, [(i, 0) for i in range(1, 8)], "in_star"),
+          gg.digraph(6, [], "empty6"), gg.digraph(1, [], "single")]
+    for n, m, sd in ((20, 30, 1), (30, 45, 2), (40, 160, 3), (60, 110, 4), (80, 260, 5)):
+        gs.append(gg.random_digraph(n, m, sd))
+    gs += [gg.oriented(gg.ba(70, 2, 3), 4), gg.oriented(gg.rmat(6, 4, seed=5), 6, both=0.1)]
+    return [(d.name, (d.offsets, d.cols)) for d in gs]
 
 
 def as_dict(L, n):
@@ -68,7 +49,8 @@ def as_dict(L, n):
 
 def test_hand_worked_example():
     fx = json.load(open(os.path.join(HERE, "golden", "hand_example_directed_4v.json")))
-    off, col = digraph(fx["n"], fx["arcs"])
+    d = gg.digraph(fx["n"], fx["arcs"])
+    off, col = d.offsets, d.cols
     ix = oracle.DirectedIndex(off, col)
     assert ix.order().tolist() == fx["degree_order"]
     Lin, Lout = as_dict(ix.labels_in(), 4), as_dict(ix.labels_out(), 4)
@@ -96,8 +78,8 @@ def test_distances_and_closed_form(name, g):
 
 
 def test_degree_order_counts_in_and_out_arcs():
-    off, col = random_digraph(70, 0.05, 9)
-    n = 70
+    d = gg.random_digraph(70, 240, 9)
+    off, col, n = d.offsets, d.cols, 70
     indeg = np.bincount(col.astype(np.int64), minlength=n)
     deg = np.diff(off.astype(np.int64)) + indeg
     expect = np.lexsort((np.arange(n), -deg))
@@ -121,8 +103,8 @@ def test_symmetric_digraph_is_the_undirected_method(g):
 @pytest.mark.parametrize("seed", [11, 12, 13])
 def test_minimality_drop_one(seed):
     """Thm 4.2 along arcs: every entry is needed by some pair."""
-    off, col = random_digraph(18, 0.12, seed)
-    n = 18
+    d = gg.random_digraph(18, 40, seed)
+    off, col, n = d.offsets, d.cols, 18
     D = brute.apsp_directed(off, col)
     ix = oracle.DirectedIndex(off, col)
     Lin, Lout = as_dict(ix.labels_in(), n), as_dict(ix.labels_out(), n)
@@ -144,7 +126,8 @@ def test_minimality_drop_one(seed):
 
 
 def test_bad_inputs_and_range():
-    off, col = digraph(4, [(0, 1), (1, 2)])
+    d = gg.digraph(4, [(0, 1), (1, 2)])
+    off, col = d.offsets, d.cols
     with pytest.raises(oracle.OracleError) as e:
         oracle.DirectedIndex(off, col, order=np.array([0, 1, 1, 3], dtype=np.uint32))
     assert e.value.code == oracle.E_ORDER
@@ -153,10 +136,12 @@ def test_bad_inputs_and_range():
     with pytest.raises(oracle.OracleError) as e:
         oracle.DirectedIndex(off, bad)
     assert e.value.code == oracle.E_INVAL
-    off, col = digraph(300, [(i, i + 1) for i in range(299)])
+    d = gg.digraph(300, [(i, i + 1) for i in range(299)])
+    off, col = d.offsets, d.cols
     with pytest.raises(oracle.OracleError) as e:
         oracle.DirectedIndex(off, col)
     assert e.value.code == oracle.E_RANGE
-    off, col = digraph(255, [(i, i + 1) for i in range(254)])
+    d = gg.digraph(255, [(i, i + 1) for i in range(254)])
+    off, col = d.offsets, d.cols
     ix = oracle.DirectedIndex(off, col)
     assert ix.query(0, 254) == 254 and ix.query(254, 0) == INF
