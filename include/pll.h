@@ -487,6 +487,56 @@ PLL_API int pll_path_query(const pll_paths *p, const uint32_t *src, const uint32
 PLL_API void pll_paths_free(pll_paths *p);
 
 /*
+ * Directed graphs (Sec. 6, "Directed Graphs"): two labels per vertex, L_IN(v)
+ * = {(u, d(u, v))} and L_OUT(v) = {(u, d(v, u))}, from a pruned BFS along the
+ * arcs and one against them for every vertex in rank order; d(s, t) is the
+ * least d(s, u) + d(u, t) over hubs u of L_OUT(s) and L_IN(t). There are no
+ * bit-parallel labels (their masks need edges both ways), so opts->t must be
+ * 0.
+ *
+ * pll_build_directed -- builds a directed index.
+ *   offsets, cols  device; out-neighbour CSR: the arcs u -> cols[e] for e in
+ *                  [offsets[u], offsets[u + 1]), each row strictly ascending,
+ *                  no self-loops, ids < n, offsets[0] = 0, offsets[n] = nnz.
+ *                  A graph whose arcs all come in both directions gives the
+ *                  undirected labels (t = 0) in both sets.
+ *   order          device or NULL: rank -> vertex; NULL = descending in- plus
+ *                  out-degree, ties by ascending id.
+ *   opts           t = 0; root_batch as for pll_build (0 = 1024, halved while
+ *                  n x root_batch / 8 bytes of visited bits pass 2 GiB); block,
+ *                  flags, reserved: 0. NULL = defaults.
+ *   out            receives the index; free it with pll_dfree.
+ * The labels are the unique ones the sequential method gives for this order.
+ * Synchronous. Errors: PLL_E_INVAL (malformed CSR, t != 0), PLL_E_ORDER,
+ * PLL_E_RANGE (n >= 2^24, a BFS depth of 255), PLL_E_NOMEM, PLL_E_CUDA.
+ */
+typedef struct pll_dindex pll_dindex;
+PLL_API int pll_build_directed(const uint32_t *offsets, const uint32_t *cols, uint32_t n,
+                               uint64_t nnz, const uint32_t *order, const pll_build_opts *opts,
+                               void *stream, pll_dindex **out);
+
+/* pll_dquery -- d(src[i], dst[i]) along arcs into out[i] (device uint8, 255 =
+ * unreachable). src, dst: device uint32[q], caller ids. Synchronous. Errors:
+ * PLL_E_INVAL (id >= n; those answers are 255), PLL_E_RANGE (a finite
+ * distance >= 255), PLL_E_CUDA. */
+PLL_API int pll_dquery(const pll_dindex *idx, const uint32_t *src, const uint32_t *dst, uint64_t q,
+                       uint8_t *out, void *stream);
+
+/* Entry counts of L_IN and L_OUT. */
+PLL_API int pll_dlabel_entries(const pll_dindex *idx, uint64_t *in_entries, uint64_t *out_entries);
+
+/* pll_dexport_labels -- host copy of L_IN (which = 0) or L_OUT (which = 1)
+ * in the layout of pll_export_labels: offsets[n + 1] by caller id, hub ranks
+ * ascending, distances. Synchronous. */
+PLL_API int pll_dexport_labels(const pll_dindex *idx, int which, uint64_t *offsets, uint32_t *hubs,
+                               uint8_t *dists);
+
+/* pll_dexport_order -- host order[n]: rank -> caller vertex id. */
+PLL_API int pll_dexport_order(const pll_dindex *idx, uint32_t *order);
+
+PLL_API void pll_dfree(pll_dindex *idx);
+
+/*
  * The index as a file (the paper answers queries from a disk-resident index,
  * Sec. 6; here the file is an image to keep and load, not to query in place).
  *

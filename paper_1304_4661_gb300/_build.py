@@ -32,6 +32,7 @@ CU_SOURCES = [
     "k_learned.cu",
     "pll_io.cu",
     "pll_paths.cu",
+    "pll_directed.cu",
 ]
 
 

@@ -33,6 +33,8 @@ SYMBOLS = [
     "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs",
     "pll_paths_create", "pll_paths_parents", "pll_path_offsets", "pll_path_query",
     "pll_paths_free",
+    "pll_build_directed", "pll_dquery", "pll_dlabel_entries", "pll_dexport_labels",
+    "pll_dexport_order", "pll_dfree",
 ]
 MLP_NPARAM = 4801
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -173,6 +175,18 @@ def load(build_if_missing: bool = True):
     lib.pll_path_query.argtypes = [vp, vp, vp, u64, vp, u64, vp, vp]
     lib.pll_paths_free.restype = None
     lib.pll_paths_free.argtypes = [vp]
+    lib.pll_build_directed.restype = i32
+    lib.pll_build_directed.argtypes = [vp, vp, u32, u64, vp, C.POINTER(BuildOpts), vp, pp]
+    lib.pll_dquery.restype = i32
+    lib.pll_dquery.argtypes = [vp, vp, vp, u64, vp, vp]
+    lib.pll_dlabel_entries.restype = i32
+    lib.pll_dlabel_entries.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    lib.pll_dexport_labels.restype = i32
+    lib.pll_dexport_labels.argtypes = [vp, i32, vp, vp, vp]
+    lib.pll_dexport_order.restype = i32
+    lib.pll_dexport_order.argtypes = [vp, vp]
+    lib.pll_dfree.restype = None
+    lib.pll_dfree.argtypes = [vp]
     lib.pll_test_fail_alloc.restype = None
     lib.pll_test_fail_alloc.argtypes = [C.c_int64]
     lib.pll_test_live_allocs.restype = C.c_int64
@@ -416,6 +430,69 @@ class Index:
         s = Stats()
         _check(load().pll_get_stats(self._h, C.byref(s)), "pll_get_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class DirectedIndex:
+    """pll_build_directed / pll_dquery: a directed-graph index (Sec. 6) on
+    the current CUDA device. offsets/cols are CUDA tensors of the
+    out-neighbour CSR."""
+
+    def __init__(self, offsets, cols, order=None, root_batch: int = 0, stream=None):
+        self._lib = load()
+        self.n = int(offsets.shape[0]) - 1
+        nnz = int(cols.shape[0])
+        opts = BuildOpts(0, root_batch, 0, 0, 0)
+        h = C.c_void_p()
+        _check(self._lib.pll_build_directed(_dptr(offsets), _dptr(cols) if nnz else None, self.n, nnz,
+                                            _dptr(order) if order is not None else None, C.byref(opts),
+                                            _stream_handle(stream), C.byref(h)), "pll_build_directed")
+        self._h = h.value
+
+    def query(self, src, dst, stream=None):
+        """d(src[i], dst[i]) along arcs: CUDA uint8 tensor (synchronous)."""
+        import torch
+        q = int(src.shape[0])
+        out = torch.empty(q, dtype=torch.uint8, device=src.device)
+        if q:
+            _check(self._lib.pll_dquery(self._h, _dptr(src), _dptr(dst), q, _dptr(out),
+                                        _stream_handle(stream)), "pll_dquery")
+        return out
+
+    def entries(self):
+        a, b = C.c_uint64(0), C.c_uint64(0)
+        _check(self._lib.pll_dlabel_entries(self._h, C.byref(a), C.byref(b)), "pll_dlabel_entries")
+        return int(a.value), int(b.value)
+
+    def _labels(self, which: int) -> Labels:
+        tot = self.entries()[which]
+        off = np.empty(self.n + 1, dtype=np.uint64)
+        hubs = np.empty(max(tot, 1), dtype=np.uint32)
+        dists = np.empty(max(tot, 1), dtype=np.uint8)
+        _check(self._lib.pll_dexport_labels(self._h, which, off.ctypes.data, hubs.ctypes.data,
+                                            dists.ctypes.data), "pll_dexport_labels")
+        return Labels(off, hubs[:tot], dists[:tot])
+
+    def labels_in(self) -> Labels:
+        return self._labels(0)
+
+    def labels_out(self) -> Labels:
+        return self._labels(1)
+
+    def order(self) -> np.ndarray:
+        out = np.empty(max(self.n, 1), dtype=np.uint32)
+        _check(self._lib.pll_dexport_order(self._h, out.ctypes.data), "pll_dexport_order")
+        return out[: self.n]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pll_dfree(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Paths:

@@ -7,8 +7,9 @@ calls it through the C ABI twice in a row (the scratch array keeps the last
 call's contents, so the second call checks that what must start at zero is
 cleared) and compares every value with the bit-parallel labels that the
 allocating entry point pll_build exports for the same order and t. The file
-is collected last so that a run stopping at its first failure has already run
-every other test; it passes alone and after the others.
+is collected after the others but the directed-graph tests, so that a run
+stopping at its first failure has already run the tests before it; it passes
+alone and after the others.
 """
 import ctypes as C
 
