@@ -846,6 +846,67 @@ def run_paths(args, ws, rank, local):
         print(json.dumps(outj), flush=True)
 
 
+def run_directed(args, ws, rank, local):
+    """Directed graphs (Sec. 6): pll_build_directed on an R-MAT graph whose
+    edges are oriented at random (30 % both ways), then 1M uniform pairs
+    through pll_dquery."""
+    import numpy as np
+    import torch
+
+    from paper_1304_4661_gb300 import graphgen as gg
+    from paper_1304_4661_gb300 import pll
+
+    torch.cuda.set_device(local)
+    pll.load()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    scale = args.directed_scale
+    d = gg.oriented(gg.rmat(scale, 16, seed=1), 2)
+    d_off, d_col = dev(d.offsets), dev(d.cols)
+    for _ in range(args.warmup):
+        pll.DirectedIndex(d_off, d_col).close()
+    bt = []
+    barrier(ws)
+    for i in range(args.steps):
+        ms, ix = timed(lambda: pll.DirectedIndex(d_off, d_col))
+        bt.append(ms)
+        ent = ix.entries()
+        if i < args.steps - 1:
+            ix.close()  # the last one answers the queries
+    barrier(ws)
+    mean_ms = max_over_ranks(ws, statistics.mean(bt))
+    q = 1_000_000
+    s, u = gg.pairs(d.n, q, 3)
+    ds, du = dev(s), dev(u)
+    for _ in range(3):
+        ix.query(ds, du)
+    qms = statistics.mean(timed(lambda: ix.query(ds, du))[0] for _ in range(5))
+    ix.close()
+    outj = {"metric": f"Directed index build (Sec. 6) on oriented R-MAT-{scale}: seconds per build",
+            "value": round(mean_ms / 1e3, 4), "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(mean_ms, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"R-MAT-{scale} (seed 1, ef 16), each edge one way at random, 30 % both "
+                                   f"ways (seed 2); {d.n} vertices, {d.nnz} arcs; 1M uniform pairs (seed 3)"},
+            "label_entries_in": ent[0], "label_entries_out": ent[1],
+            "queries_per_s": round(q / (qms * 1e-3), 1)}
+    if rank == 0:
+        print(json.dumps(outj), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_baseline(args, scale=None):
     """The oracle as it stands (single thread) on a bounded sample: a full
@@ -909,7 +970,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned", "variants", "paths"], default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "serve", "learned", "variants", "paths", "directed"], default="rmat20")
     ap.add_argument("--root-batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--latency-samples", type=int, default=2000)
@@ -922,15 +983,17 @@ def main():
     ap.add_argument("--serve-clients", type=int, default=4)
     ap.add_argument("--learned-graphs", type=int, default=200)
     ap.add_argument("--learned-epochs", type=int, default=4)
+    ap.add_argument("--directed-scale", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload in ("batch256", "serve", "learned", "variants", "paths"):
+    if args.workload in ("batch256", "serve", "learned", "variants", "paths", "directed"):
         ws, rank, local = dist_setup()
         {"batch256": run_batch, "serve": run_serve, "learned": run_learned,
-         "variants": run_variants, "paths": run_paths}[args.workload](args, ws, rank, local)
+         "variants": run_variants, "paths": run_paths,
+         "directed": run_directed}[args.workload](args, ws, rank, local)
         return
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup() if args.impl == "ours" else (
