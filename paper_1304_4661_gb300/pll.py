@@ -509,8 +509,14 @@ class Paths:
                                           nnz, _stream_handle(stream), C.byref(h)), "pll_paths_create")
         self._h = h.value
 
+    def _live(self):
+        # the C object borrows the index's device arrays
+        if not getattr(self.index, "_h", None) or not getattr(self, "_h", None):
+            raise RuntimeError("Paths used after its Index (or itself) was closed")
+
     def parents(self) -> np.ndarray:
         """Parent (caller id) of every label entry, in the layout of Index.labels()."""
+        self._live()
         tot = self.index.label_entries()
         out = np.empty(max(tot, 1), dtype=np.uint32)
         _check(self._lib.pll_paths_parents(self._h, out.ctypes.data), "pll_paths_parents")
@@ -519,6 +525,7 @@ class Paths:
     def offsets(self, src, dst, stream=None):
         """pll_path_offsets: (path_off int64 CUDA [q + 1], total)."""
         import torch
+        self._live()
         q = int(src.shape[0])
         off = torch.empty(q + 1, dtype=torch.int64, device=src.device)
         tot = C.c_uint64(0)
@@ -532,6 +539,7 @@ class Paths:
         path (caller ids) in path[path_off[i]:path_off[i + 1]]. Without
         path_off the slots come from offsets()."""
         import torch
+        self._live()
         q = int(src.shape[0])
         if path_off is None:
             path_off, cap = self.offsets(src, dst, stream)
