@@ -77,6 +77,22 @@ def test_distances_and_closed_form(name, g):
         assert as_dict(ix.labels_out(), n) == Lout, name
 
 
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_every_digraph_up_to_4_vertices(n):
+    """Every labelled digraph without self-loops on n vertices (2^(n(n-1))
+    of them): distances and both label sets against their closed forms."""
+    pairs = [(a, b) for a in range(n) for b in range(n) if a != b]
+    s = np.repeat(np.arange(n, dtype=np.uint32), n)
+    t = np.tile(np.arange(n, dtype=np.uint32), n)
+    for mask in range(1 << len(pairs)):
+        d = gg.digraph(n, [pairs[i] for i in range(len(pairs)) if mask >> i & 1])
+        D = brute.apsp_directed(d.offsets, d.cols)
+        ix = oracle.DirectedIndex(d.offsets, d.cols)
+        assert np.array_equal(ix.query_batch(s, t).astype(np.int64), D.reshape(-1)), mask
+        Lin, Lout = brute.canonical_directed(D, ix.order())
+        assert as_dict(ix.labels_in(), n) == Lin and as_dict(ix.labels_out(), n) == Lout, mask
+
+
 def test_degree_order_counts_in_and_out_arcs():
     d = gg.random_digraph(70, 240, 9)
     off, col, n = d.offsets, d.cols, 70

@@ -77,6 +77,24 @@ def test_exhaustive_5_vertices(t):
         assert labels_dict(ix) == brute.canonical(D, ix.order(), inX), g.name
 
 
+@pytest.mark.parametrize("t", [0, 1, 3])
+def test_every_graph_up_to_7_vertices(t):
+    """Every graph on at most 7 vertices up to isomorphism (the 1,253 graphs of
+    the graph atlas, in its labelling): distances and the canonical label set,
+    with the bit-parallel stage taking up to t roots."""
+    nx = pytest.importorskip("networkx")
+    for G in nx.graph_atlas_g():
+        n = G.number_of_nodes()
+        e = np.asarray(list(G.edges()), dtype=np.int64).reshape(-1, 2)
+        g = gg.from_edges(n, e[:, 0], e[:, 1], f"atlas{n}")
+        D = brute.apsp(g.offsets, g.cols)
+        ix = oracle.Index(g.offsets, g.cols, t)
+        s, u = all_pairs(n)
+        assert np.array_equal(ix.query_batch(s, u).reshape(n, n).astype(np.int64), D), G.edges()
+        _, inX = ix.rank_inX()
+        assert labels_dict(ix) == brute.canonical(D, ix.order(), inX), G.edges()
+
+
 # -------------------------------------------------- canonical label set (O1)
 @pytest.mark.parametrize("t", [0, 1, 3, 16])
 @pytest.mark.parametrize("g", graphs.small_family(), ids=lambda g: g.name)
