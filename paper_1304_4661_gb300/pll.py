@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -269,6 +270,10 @@ class Index:
         self.n = n
         self.t = t
         self.graphs = 1
+        self._users = weakref.WeakSet()  # Server / Paths objects that borrow the index
+
+    def _lend(self, user):
+        self._users.add(user)
 
     # ------------------------------------------------------------- build
     @classmethod
@@ -317,7 +322,11 @@ class Index:
         return ix
 
     def close(self):
+        """pll_free. Refused while a Server or Paths object built on this
+        index is still open (they borrow its device arrays)."""
         if getattr(self, "_h", None):
+            if any(getattr(u, "_h", None) for u in getattr(self, "_users", ())):
+                raise RuntimeError("stop the Server / close the Paths objects of this index first")
             load().pll_free(self._h)
             self._h = None
 
@@ -508,6 +517,7 @@ class Paths:
         _check(self._lib.pll_paths_create(index._h, _dptr(offsets), _dptr(cols) if nnz else None, n,
                                           nnz, _stream_handle(stream), C.byref(h)), "pll_paths_create")
         self._h = h.value
+        index._lend(self)
 
     def _live(self):
         # the C object borrows the index's device arrays
@@ -591,6 +601,7 @@ class Server:
         _check(self._lib.pll_server_start(index._h, C.byref(o), C.byref(h)), "pll_server_start")
         self._h = h.value
         self._live = {}
+        index._lend(self)
 
     def submit(self, src, dst) -> int:
         s, sp = _hptr(src, np.uint32)

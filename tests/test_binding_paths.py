@@ -21,3 +21,18 @@ def test_paths_after_index_closed_raises():
     with pytest.raises(RuntimeError):
         p.query([], [])
     p._h = None  # nothing to free
+
+
+def test_index_close_refused_while_borrowed():
+    ix = pll.Index.__new__(pll.Index)
+    pll.Index.__init__(ix, 1234, 3, 0)  # a handle that is never passed to the library
+
+    class _User:
+        _h = 1
+
+    u = _User()
+    ix._lend(u)
+    with pytest.raises(RuntimeError):
+        ix.close()
+    u._h = None  # the borrower closed: close() would now free the handle
+    ix._h = None  # but this one is fake, so drop it instead
