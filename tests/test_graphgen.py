@@ -99,3 +99,43 @@ def test_poisson_arrivals():
     # exponential gaps of mean 1 ms: mean and coefficient of variation near 1
     assert abs(gaps.mean() - 1000.0) < 30
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05
+
+
+def _arcs(d):
+    rows = np.repeat(np.arange(d.n), np.diff(d.offsets.astype(np.int64)))
+    return set(zip(rows.tolist(), d.cols.tolist()))
+
+
+def test_digraph_csr_shape():
+    d = gg.digraph(5, [(0, 1), (0, 1), (2, 2), (3, 0), (0, 4), (4, 3)])
+    assert d.offsets.tolist() == [0, 2, 2, 2, 3, 4]
+    assert d.cols.tolist() == [1, 4, 0, 3]  # repeats and the self-loop dropped, rows ascending
+    e = gg.digraph(3, [])
+    assert e.offsets.tolist() == [0, 0, 0, 0] and e.nnz == 0
+
+
+def test_random_digraph_seeded():
+    a, b, c = gg.random_digraph(200, 1000, 3), gg.random_digraph(200, 1000, 3), gg.random_digraph(200, 1000, 4)
+    assert np.array_equal(a.cols, b.cols) and np.array_equal(a.offsets, b.offsets)
+    assert not np.array_equal(a.cols, c.cols)
+    arcs = _arcs(a)
+    assert all(u != v for u, v in arcs) and 900 < len(arcs) <= 1000
+    for v in range(a.n):
+        row = a.cols[a.offsets[v]:a.offsets[v + 1]]
+        assert (np.diff(row.astype(np.int64)) > 0).all()
+
+
+def test_oriented_keeps_every_edge_once_or_both_ways():
+    g = gg.ba(2000, 3, 5)
+    d = gg.oriented(g, 7, both=0.3)
+    arcs = _arcs(d)
+    und = _arcs(gg.Digraph(g.n, g.offsets, g.cols))
+    assert arcs <= und
+    edges = {(u, v) for u, v in und if u < v}
+    two = sum(1 for u, v in edges if (u, v) in arcs and (v, u) in arcs)
+    assert all((u, v) in arcs or (v, u) in arcs for u, v in edges)
+    assert abs(two / len(edges) - 0.3) < 0.03
+    one_fwd = sum(1 for u, v in edges if (u, v) in arcs and (v, u) not in arcs)
+    one_rev = sum(1 for u, v in edges if (v, u) in arcs and (u, v) not in arcs)
+    assert abs(one_fwd - one_rev) < 0.1 * (one_fwd + one_rev)
+    assert np.array_equal(gg.oriented(g, 7, both=0.3).cols, d.cols)
