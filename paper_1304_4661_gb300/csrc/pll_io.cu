@@ -65,7 +65,7 @@ int put(FILE *f, const void *d, size_t bytes) {
 template <class T>
 int get(FILE *f, T **d, size_t count) {
     const size_t bytes = count * sizeof(T);
-    PLL_TRY(cudaMalloc(d, bytes ? bytes : 16));
+    PLL_TRY(pll::dev_malloc(d, bytes ? bytes : 16));
     const size_t chunk = 64u << 20;
     std::unique_ptr<unsigned char[]> buf(new (std::nothrow) unsigned char[bytes < chunk ? (bytes ? bytes : 1) : chunk]);
     if (!buf) return PLL_E_NOMEM;
@@ -153,8 +153,8 @@ PLL_API int pll_load(const char *path, pll_index **out) {
     ix->graphs = h.graphs;
     ix->nnz = h.nnz;
     ix->entries = h.entries;
-    PLL_TRY(cudaMalloc(&ix->d_order, n ? n * 4 : 16));
-    PLL_TRY(cudaMalloc(&ix->d_inv, n ? n * 4 : 16));
+    PLL_TRY(pll::dev_malloc(&ix->d_order, n ? n * 4 : 16));
+    PLL_TRY(pll::dev_malloc(&ix->d_inv, n ? n * 4 : 16));
     if (n) {
         PLL_TRY(cudaMemcpy(ix->d_order, order.data(), n * 4, cudaMemcpyHostToDevice));
         PLL_TRY(cudaMemcpy(ix->d_inv, inv.data(), n * 4, cudaMemcpyHostToDevice));
@@ -170,10 +170,10 @@ PLL_API int pll_load(const char *path, pll_index **out) {
     if (off[0] != 0 || off[n] != h.entries) return PLL_E_INVAL;
     for (uint64_t v = 0; v < n; ++v)
         if (off[v + 1] < off[v]) return PLL_E_INVAL;
-    PLL_TRY(cudaMalloc(&ix->d_lab_off, (n + 1) * 8));
+    PLL_TRY(pll::dev_malloc(&ix->d_lab_off, (n + 1) * 8));
     PLL_TRY(cudaMemcpy(ix->d_lab_off, off.data(), (n + 1) * 8, cudaMemcpyHostToDevice));
     PLL_CHECK(get(file.f, &ix->d_lab, h.entries));
-    PLL_TRY(cudaMalloc(&ix->d_qerr, 16));
+    PLL_TRY(pll::dev_malloc(&ix->d_qerr, 16));
     PLL_TRY(cudaMemset(ix->d_qerr, 0, 16));
     ix->stats.n = h.n;
     ix->stats.t = h.t;
