@@ -459,8 +459,10 @@ void orc_export_labels(const orc_index *ix, uint64_t *offsets, uint32_t *hubs, u
     uint64_t p = 0;
     for (uint32_t v = 0; v < ix->n; ++v) {
         offsets[v] = p;
-        memcpy(hubs + p, ix->hub[v], (size_t)ix->len[v] * sizeof(uint32_t));
-        memcpy(dists + p, ix->dist[v], ix->len[v]);
+        if (ix->len[v]) { /* an empty label has no arrays (memcpy wants real pointers) */
+            memcpy(hubs + p, ix->hub[v], (size_t)ix->len[v] * sizeof(uint32_t));
+            memcpy(dists + p, ix->dist[v], ix->len[v]);
+        }
         p += ix->len[v];
     }
     offsets[ix->n] = p;
@@ -484,7 +486,7 @@ void orc_export_bp_roots(const orc_index *ix, uint32_t *roots, uint32_t *cnt, ui
 void orc_export_parents(const orc_index *ix, uint32_t *parents) {
     uint64_t p = 0;
     for (uint32_t v = 0; v < ix->n; ++v) {
-        memcpy(parents + p, ix->par[v], (size_t)ix->len[v] * sizeof(uint32_t));
+        if (ix->len[v]) memcpy(parents + p, ix->par[v], (size_t)ix->len[v] * sizeof(uint32_t));
         p += ix->len[v];
     }
 }
@@ -920,8 +922,10 @@ void orc_dexport(const orc_dindex *ix, int which, uint64_t *offsets, uint32_t *h
     uint64_t p = 0;
     for (uint32_t v = 0; v < ix->n; ++v) {
         offsets[v] = p;
-        memcpy(hubs + p, L->hub[v], (size_t)L->len[v] * sizeof(uint32_t));
-        memcpy(dists + p, L->dist[v], L->len[v]);
+        if (L->len[v]) {
+            memcpy(hubs + p, L->hub[v], (size_t)L->len[v] * sizeof(uint32_t));
+            memcpy(dists + p, L->dist[v], L->len[v]);
+        }
         p += L->len[v];
     }
     offsets[ix->n] = p;
