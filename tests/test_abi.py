@@ -53,3 +53,32 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert lib.pll_label_entries(None, None) == pll.PLL_E_INVAL
     assert lib.pll_get_stats(None, None) == pll.PLL_E_INVAL
     lib.pll_free(None)
+
+
+def test_path_and_directed_argument_checks_without_a_gpu():
+    """The host-side checks of the shortest-path and directed entry points
+    return before any CUDA call."""
+    lib = pll.load()
+    out = C.c_void_p()
+    assert lib.pll_paths_create(None, None, None, 0, 0, None, C.byref(out)) == pll.PLL_E_INVAL
+    assert lib.pll_paths_create(None, None, None, 0, 0, None, None) == pll.PLL_E_INVAL
+    assert lib.pll_paths_parents(None, None) == pll.PLL_E_INVAL
+    tot = C.c_uint64(0)
+    assert lib.pll_path_offsets(None, None, None, 1, None, C.byref(tot), None) == pll.PLL_E_INVAL
+    assert lib.pll_path_query(None, None, None, 1, None, 0, None, None) == pll.PLL_E_INVAL
+    lib.pll_paths_free(None)
+    opts = pll.BuildOpts(0, 0, 0, 0, 0)
+    assert lib.pll_build_directed(None, None, 0, 0, None, C.byref(opts), None, None) == pll.PLL_E_INVAL
+    assert lib.pll_build_directed(None, None, 1 << 24, 0, None, C.byref(opts), None,
+                                  C.byref(out)) == pll.PLL_E_RANGE
+    assert lib.pll_build_directed(None, None, 0, 1, None, C.byref(opts), None, C.byref(out)) == pll.PLL_E_INVAL
+    assert lib.pll_build_directed(None, None, 5, 0, None, C.byref(opts), None, C.byref(out)) == pll.PLL_E_INVAL
+    for bad in (pll.BuildOpts(1, 0, 0, 0, 0), pll.BuildOpts(0, 0, 0, 1, 0), pll.BuildOpts(0, 0, 0, 0, 1)):
+        assert lib.pll_build_directed(None, None, 0, 0, None, C.byref(bad), None, C.byref(out)) == pll.PLL_E_INVAL
+    assert out.value is None
+    assert lib.pll_dquery(None, None, None, 1, None, None) == pll.PLL_E_INVAL
+    a, b = C.c_uint64(0), C.c_uint64(0)
+    assert lib.pll_dlabel_entries(None, C.byref(a), C.byref(b)) == pll.PLL_E_INVAL
+    assert lib.pll_dexport_labels(None, 0, None, None, None) == pll.PLL_E_INVAL
+    assert lib.pll_dexport_order(None, None) == pll.PLL_E_INVAL
+    lib.pll_dfree(None)
