@@ -16,7 +16,7 @@ from paper_1304_4661_gb300 import graphgen as gg
 from paper_1304_4661_gb300 import pll
 
 from . import graphs
-from .gpu_util import dev_u32, gpu_build, same_labels
+from .gpu_util import dev_u32, first_label_diff, gpu_build, same_labels
 
 pytestmark = pytest.mark.gpu
 
@@ -54,9 +54,10 @@ def test_small_digraphs_exact(d, root_batch):
         ix = build(d, order, root_batch)
         ref = oracle.DirectedIndex(d.offsets, d.cols, order=order)
         assert np.array_equal(ix.order(), ref.order())
-        assert same_labels(ix.labels_in(), ref.labels_in())
-        assert same_labels(ix.labels_out(), ref.labels_out())
-        assert ix.entries() == (len(ref.labels_in().hubs), len(ref.labels_out().hubs))
+        gi, ri, go, ro = ix.labels_in(), ref.labels_in(), ix.labels_out(), ref.labels_out()
+        assert same_labels(gi, ri), ("L_IN", first_label_diff(gi, ri, n))
+        assert same_labels(go, ro), ("L_OUT", first_label_diff(go, ro, n))
+        assert ix.entries() == (len(ri.hubs), len(ro.hubs))
         s = np.repeat(np.arange(n, dtype=np.uint32), n)
         t = np.tile(np.arange(n, dtype=np.uint32), n)
         assert np.array_equal(gpu_dquery(ix, s, t), ref.query_batch(s, t))
@@ -70,8 +71,9 @@ def test_larger_digraphs(d):
     ix = build(d)
     ref = oracle.DirectedIndex(d.offsets, d.cols)
     assert np.array_equal(ix.order(), ref.order())
-    assert same_labels(ix.labels_in(), ref.labels_in())
-    assert same_labels(ix.labels_out(), ref.labels_out())
+    gi, ri, go, ro = ix.labels_in(), ref.labels_in(), ix.labels_out(), ref.labels_out()
+    assert same_labels(gi, ri), ("L_IN", first_label_diff(gi, ri, d.n))
+    assert same_labels(go, ro), ("L_OUT", first_label_diff(go, ro, d.n))
     s, t = gg.pairs(d.n, 20011, 5)
     assert np.array_equal(gpu_dquery(ix, s, t), ref.query_batch(s, t))
 
