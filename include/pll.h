@@ -5,7 +5,9 @@
  * Landmark Labeling", SIGMOD 2013).
  *
  * Problem (Sec. 3.2): given an undirected, unweighted graph G = (V, E), build
- * an index that answers the distance d_G(s, t) for any pair exactly.
+ * an index that answers the distance d_G(s, t) for any pair exactly. Sec. 6
+ * variants: shortest paths over such an index (pll_paths_*, pll_path_*) and
+ * directed graphs (pll_build_directed, pll_dquery, pll_d*).
  *
  * Conventions shared by every entry point
  *   - Graphs are symmetric CSR: offsets[n + 1] (uint32, offsets[0] = 0,
