@@ -842,6 +842,8 @@ def run_paths(args, ws, rank, local):
             "gpu_launches": 3 * args.steps}
     P.close()
     ix.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        outj["cpu_baseline"] = cpu_paths_sample()
     if rank == 0:
         print(json.dumps(outj), flush=True)
 
@@ -903,6 +905,8 @@ def run_directed(args, ws, rank, local):
                                    f"ways (seed 2); {d.n} vertices, {d.nnz} arcs; 1M uniform pairs (seed 3)"},
             "label_entries_in": ent[0], "label_entries_out": ent[1],
             "queries_per_s": round(q / (qms * 1e-3), 1)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        outj["cpu_baseline"] = cpu_directed_sample()
     if rank == 0:
         print(json.dumps(outj), flush=True)
 
@@ -926,6 +930,38 @@ def cpu_baseline(args, scale=None):
             "queries_per_s": round(1_000_000 / tq, 1),
             "sample": f"full oracle build of R-MAT scale {scale} (ef 16, seed 1, t=64, "
                       f"{g.n} vertices, {g.nnz} arcs), then 1M uniform queries; single thread"}
+
+
+def cpu_paths_sample(scale: int = 16, q: int = 20000):
+    """The oracle's path restoration (Sec. 6) as it stands, single-threaded,
+    on a bounded sample: R-MAT at `scale` (t = 64), q uniform pairs."""
+    import oracle
+    from paper_1304_4661_gb300 import graphgen as gg
+    g = gg.rmat(scale, 16, seed=1)
+    ix = oracle.Index(g.offsets, g.cols, 64)
+    s, u = gg.pairs(g.n, q, 3)
+    t0 = time.perf_counter()
+    verts = sum(len(ix.path(int(a), int(b))) for a, b in zip(s, u))
+    dt = time.perf_counter() - t0
+    return {"value": round(q / dt, 1), "unit": "paths/s", "cores": 1, "kind": "oracle",
+            "path_vertices_per_s": round(verts / dt, 1),
+            "sample": f"{q} uniform pairs on R-MAT scale {scale} (ef 16, seed 1, t = 64, oracle index "
+                      f"built beforehand, not timed); one oracle call per pair; single thread"}
+
+
+def cpu_directed_sample(scale: int = 14):
+    """The oracle's directed build (Sec. 6) as it stands, single-threaded, on
+    an oriented R-MAT of the given scale."""
+    import oracle
+    from paper_1304_4661_gb300 import graphgen as gg
+    d = gg.oriented(gg.rmat(scale, 16, seed=1), 2)
+    t0 = time.perf_counter()
+    ix = oracle.DirectedIndex(d.offsets, d.cols)
+    dt = time.perf_counter() - t0
+    return {"value": round(dt, 3), "unit": "s", "cores": 1, "kind": "oracle",
+            "label_entries": [len(ix.labels_in().hubs), len(ix.labels_out().hubs)],
+            "sample": f"full oracle directed build of oriented R-MAT scale {scale} (ef 16, seed 1, "
+                      f"orientation seed 2, 30 % both ways; {d.n} vertices, {d.nnz} arcs); single thread"}
 
 
 def run_reference(args, w, ws, rank):
