@@ -46,7 +46,7 @@ WORKLOADS = {
 # for the kernel source with this hash (else traffic is reported as null).
 PROFILED = {
     # ncu, all 336 + 336 sweep launches of one R-MAT-20 build at the default
-    # root batch (profiles/k_batch_sweeps_rmat20.md); valid for that launch count
+    # root batch; valid for that launch count
     "k_batch_expand": {"src_sha": "4d85bff4eab1dcd6", "launches": 336, "dram_bytes_per_launch": 798236397},
     "k_batch_test": {"src_sha": "4d85bff4eab1dcd6", "launches": 336, "dram_bytes_per_launch": 485875839},
 }

@@ -257,10 +257,13 @@ PLL_API int pll_export_order(const pll_index *idx, uint32_t *order);
  * one file-scope device array of PLL_NOALLOC_SCRATCH_BYTES, held by every GPU
  * that loads the library until the process exits; a call needs about
  * 13 * n + nnz / 64 bytes of it plus a few KiB, and returns PLL_E_RANGE if the
- * graph does not fit. The first call on a device (with that device current)
- * looks up the array's device address once; make that first call before any
- * stream capture. All calls share the array, so calls that overlap on the GPU
- * race. Synchronous.
+ * graph does not fit. Every call looks the array's device address up in the
+ * current context (nothing is cached, so a device reset between calls does no
+ * harm). Under lazy module loading (the CUDA default) the 64 MiB are reserved
+ * on a device by the first call there: make that call early, before the GPU
+ * is filled (a reservation that fails is PLL_E_NOMEM) and before any stream
+ * capture. All calls share the array, so calls that overlap on the GPU race.
+ * Synchronous.
  */
 PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *rank_cols,
                                   uint32_t n, uint64_t nnz, uint32_t t, uint8_t *d,

@@ -9,22 +9,21 @@
 // GPU that loads this library holds until the process exits.
 //
 // In host code the array's name is a host-side stand-in, not a device address,
-// so on the first call on each device (with that device current) the entry
-// point asks the runtime for the array's device address once with
-// cudaGetSymbolAddress and caches it. Every call shares the one array: the
-// parts that must start at zero are cleared on each call, and calls whose work
-// overlaps on the GPU (other streams, other threads) race on it.
-#include <mutex>
-
+// so every call, with the caller's device current, asks the runtime for the
+// array's device address with cudaGetSymbolAddress. The lookup is cheap and
+// nothing is cached: after a reset of the device (or a release and re-creation
+// of its primary context) the module is loaded again at a new address, which a
+// cached pointer would miss. With lazy module loading (the CUDA default) the
+// array itself is reserved on a device by the first call there, so make that
+// first call early, before the GPU is filled and before any stream capture.
+// Every call shares the one array: the parts that must start at zero are
+// cleared on each call, and calls whose work overlaps on the GPU (other
+// streams, other threads) race on it.
 #include "pll_internal.cuh"
 
 namespace {
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[PLL_NOALLOC_SCRATCH_BYTES];
-
-constexpr int MAX_DEVICES = 256;
-void *g_scratch_addr[MAX_DEVICES];  // device address of g_noalloc_scratch, per device
-std::mutex g_scratch_mu;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -33,18 +32,14 @@ size_t needed_bytes(uint32_t n, uint64_t nnz) {
     return 256 + up256((size_t)n) + pll::bp_scratch_bytes(n, nnz, nullptr);
 }
 
+// device address of g_noalloc_scratch in the current context; a reservation
+// that fails at a lazy module load (no memory left) is PLL_E_NOMEM
 int scratch_address(void **out) {
-    int dev = 0;
-    PLL_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAX_DEVICES) return PLL_E_CUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) return pll::cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return pll::cuda_status(e);
+    if (p == nullptr) return PLL_E_CUDA;
+    *out = p;
     return PLL_OK;
 }
 

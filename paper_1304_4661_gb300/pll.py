@@ -248,8 +248,32 @@ def bp_labels_noalloc(rank_offsets, rank_cols, t: int, d, masks, roots, cnt, S, 
     """pll_bp_labels_noalloc on CUDA tensors (outputs preallocated by the caller):
     d uint8[n * tp] (tp = t rounded up to 16), masks uint64[n * t * 2],
     roots/cnt uint32[t], S uint32[t * 64]; ids are ranks."""
+    import torch
     n = int(rank_offsets.shape[0]) - 1
     nnz = int(rank_cols.shape[0])
+    tp = (t + 15) // 16 * 16
+    # the library writes exactly these sizes: refuse anything else before the call
+    want = [("rank_offsets", rank_offsets, (torch.int32, torch.uint32), n + 1),
+            ("rank_cols", rank_cols, (torch.int32, torch.uint32), nnz),
+            ("d", d, (torch.uint8,), n * tp),
+            ("masks", masks, (torch.int64, torch.uint64), 2 * n * t),
+            ("roots", roots, (torch.int32, torch.uint32), t),
+            ("cnt", cnt, (torch.int32, torch.uint32), t),
+            ("S", S, (torch.int32, torch.uint32), 64 * t)]
+    for name, x, dtypes, numel in want:
+        if not _is_torch(x):
+            raise ValueError(f"{name}: a torch tensor is required")
+        if x.dtype not in dtypes:
+            raise ValueError(f"{name}: dtype {x.dtype}, expected one of {dtypes}")
+        if x.numel() != numel:
+            raise ValueError(f"{name}: {x.numel()} elements, expected {numel}")
+    for name, x, _, _ in want:
+        if not (x.is_cuda and x.is_contiguous()):
+            raise ValueError(f"{name}: a contiguous CUDA tensor is required")
+    dev = torch.cuda.current_device()
+    for name, x, _, _ in want:
+        if x.device.index != dev:
+            raise ValueError(f"{name}: on cuda:{x.device.index}, the current device is cuda:{dev}")
     _check(load().pll_bp_labels_noalloc(_dptr(rank_offsets), _dptr(rank_cols) if nnz else None, n,
                                         nnz, t, _dptr(d), _dptr(masks), _dptr(roots), _dptr(cnt),
                                         _dptr(S), _stream_handle(stream)), "pll_bp_labels_noalloc")

@@ -82,3 +82,41 @@ def test_path_and_directed_argument_checks_without_a_gpu():
     assert lib.pll_dexport_labels(None, 0, None, None, None) == pll.PLL_E_INVAL
     assert lib.pll_dexport_order(None, None) == pll.PLL_E_INVAL
     lib.pll_dfree(None)
+
+
+def test_noalloc_binding_refuses_wrong_outputs_without_a_gpu():
+    """bp_labels_noalloc checks every tensor's dtype and exact size before the
+    call: an undersized output would otherwise be written past its end."""
+    import torch
+    n, nnz, t = 10, 18, 16
+    tp = 16
+
+    def args(**over):
+        a = dict(rank_offsets=torch.zeros(n + 1, dtype=torch.int32),
+                 rank_cols=torch.zeros(nnz, dtype=torch.int32),
+                 d=torch.zeros(n * tp, dtype=torch.uint8),
+                 masks=torch.zeros(2 * n * t, dtype=torch.int64),
+                 roots=torch.zeros(t, dtype=torch.int32),
+                 cnt=torch.zeros(t, dtype=torch.int32),
+                 S=torch.zeros(64 * t, dtype=torch.int32))
+        a.update(over)
+        return a
+
+    def call(a):
+        pll.bp_labels_noalloc(a["rank_offsets"], a["rank_cols"], t, a["d"], a["masks"], a["roots"],
+                              a["cnt"], a["S"])
+
+    bad = [dict(d=torch.zeros(n * tp - 1, dtype=torch.uint8)),
+           dict(d=torch.zeros(n * t, dtype=torch.int32)),
+           dict(masks=torch.zeros(2 * n * t - 2, dtype=torch.int64)),
+           dict(masks=torch.zeros(2 * n * t, dtype=torch.float64)),
+           dict(roots=torch.zeros(t - 1, dtype=torch.int32)),
+           dict(cnt=torch.zeros(t, dtype=torch.int64)),
+           dict(S=torch.zeros(64 * t - 64, dtype=torch.int32)),
+           dict(rank_cols=torch.zeros(nnz, dtype=torch.int64))]
+    for over in bad:
+        with pytest.raises(ValueError, match="dtype|elements"):
+            call(args(**over))
+    # right sizes on the host are refused too: the outputs must be CUDA tensors
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        call(args())

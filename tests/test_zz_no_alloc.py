@@ -6,7 +6,10 @@ it keeps its scratch in a fixed device array inside the library. This test
 calls it through the C ABI twice in a row (the scratch array keeps the last
 call's contents, so the second call checks that what must start at zero is
 cleared) and compares every value with the bit-parallel labels that the
-allocating entry point pll_build exports for the same order and t. The file
+allocating entry point pll_build exports for the same order and t. The
+second call runs with the library's allocation-failure hook set so that any
+allocation it made would fail, and the library's live-allocation count and
+torch's allocated bytes must be the same after each call as before. The file
 is collected after the others but the directed-graph tests, so that a run
 stopping at its first failure has already run the tests before it; it passes
 alone and after the others.
@@ -53,13 +56,26 @@ def test_noalloc_matches_pll_build_twice(make, t):
     roff, rcol, rank = rank_space_csr(g, order)
     n, tp = g.n, (t + 15) // 16 * 16
     droff, drcol = dev_u32(roff), dev_u32(rcol)
+    lib = pll.load()
     for call in range(2):
         d = torch.full((n * tp,), 7, dtype=torch.uint8, device="cuda")
         masks = torch.full((n * t * 2,), 3, dtype=torch.int64, device="cuda")
         roots = torch.zeros(t, dtype=torch.int32, device="cuda")
         cnt = torch.zeros(t, dtype=torch.int32, device="cuda")
         S = torch.zeros(t * 64, dtype=torch.int32, device="cuda")
-        pll.bp_labels_noalloc(droff, drcol, t, d, masks, roots, cnt, S)
+        torch.cuda.synchronize()
+        live, held = lib.pll_test_live_allocs(), torch.cuda.memory_allocated()
+        if call == 1:
+            # the second call runs with every allocation of the library set to
+            # fail: it must still succeed, since it allocates nothing
+            lib.pll_test_fail_alloc(0)
+        try:
+            pll.bp_labels_noalloc(droff, drcol, t, d, masks, roots, cnt, S)
+            torch.cuda.synchronize()
+        finally:
+            lib.pll_test_fail_alloc(-1)
+        assert lib.pll_test_live_allocs() == live, call
+        assert torch.cuda.memory_allocated() == held, call
         hd = d.cpu().numpy().reshape(n, tp)
         hm = masks.cpu().numpy().view(np.uint64).reshape(n, t, 2)
         assert (hd[:, t:] == 255).all(), call
