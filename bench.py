@@ -39,6 +39,7 @@ WORKLOADS = {
     # smaller R-MATs of the same family (profiling, quick runs)
     "rmat19": dict(kind="rmat", scale=19, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
     "rmat18": dict(kind="rmat", scale=18, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
+    "rmat17": dict(kind="rmat", scale=17, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
     "rmat16": dict(kind="rmat", scale=16, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
 }
 

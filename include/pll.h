@@ -110,6 +110,11 @@ typedef struct pll_stats {
     uint64_t candidates;         /* candidates passed from expand to test */
     uint32_t graphs;             /* graphs in the index (1 unless pll_build_batch) */
     uint32_t reserved32;
+    /* buffer growth of the pruned stage (none of it changes the labels) */
+    uint64_t redone_batches;     /* batches run again after a buffer overflowed */
+    uint64_t pool_regrows;       /* times the label pool was moved to a larger one */
+    uint64_t table_fallbacks;    /* batches whose root tables did not all fit
+                                    (those roots' labels were binary-searched) */
 } pll_stats;
 
 /*
@@ -578,6 +583,20 @@ PLL_API void pll_free(pll_index *idx);
  */
 PLL_API void pll_test_fail_alloc(int64_t k);
 PLL_API int64_t pll_test_live_allocs(void);
+
+/*
+ * Test hook for the buffer-growth paths of the pruned stage; the paper has no
+ * counterpart. pll_test_capacities(cand, out, pool, tables) sets the initial
+ * sizes, in entries, of the candidate buffer, the pre-cleanup tuple buffer,
+ * the label pool and the root-table pool of every later build (0 keeps the
+ * library's own sizing, which is the default). With cand or out set, buffers
+ * are not grown ahead of demand, so a batch that overflows one is run again
+ * with a larger one; with tables set, the root-table pool keeps that size for
+ * the whole build, so the roots whose tables do not fit have their labels
+ * binary-searched. None of this changes the labels. Process-wide; the
+ * counts appear in pll_stats.
+ */
+PLL_API void pll_test_capacities(uint64_t cand, uint64_t out, uint64_t pool, uint64_t tables);
 
 /* Static, human-readable text for a status code. */
 PLL_API const char *pll_status_str(int status);

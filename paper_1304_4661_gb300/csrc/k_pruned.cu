@@ -21,11 +21,18 @@
 //           4.5.1 ("Querying"), so a prune test costs O(|L(u)|) probes -- and
 //           two 64-bit feasibility masks over the bit-parallel roots.
 //   expand  one warp per entry (u, k, d) of the level: read u's neighbours 32
-//           per step and claim the unvisited ones with an atomicOr on a
-//           vertex-major bitmap [n][W] holding one bit per root of the batch.
-//           Each lane then runs the cheap part of the prune test on its
-//           claimed neighbour w at once (it decides ~70% of candidates on
-//           power-law graphs): bit-parallel distances only -- with
+//           per step and look each one up in the root's visited row (a bitmap
+//           [B][ceil(n / 32)], one row per root of the batch: the per-root
+//           visited set of Alg. 1, one bit per vertex, so the 32 lanes of a
+//           warp, which share the root, read neighbouring words). For a
+//           neighbour w not yet visited, the lane first runs the cheap part of
+//           the prune test (it decides ~90% of them on power-law graphs) and
+//           claims w with an atomicOr only if w survives it. A vertex the
+//           bit-parallel labels prune stays unmarked: the bit-parallel bound
+//           of a pair does not depend on the level, so if it prunes w at level
+//           d + 1 it prunes w again at any later level where w is reached, and
+//           leaving the bit clear changes no label. The test: bit-parallel
+//           distances only -- with
 //           d~_i = d(v_k,r_i) + d(r_i,w), some d~_i <= d + 1 prunes (Sec. 5.3:
 //           the distance through {r_i} U S_{r_i} is at most d~_i). Rows of t
 //           bytes (padded to 16) arrive in 16-byte loads, four roots per
@@ -36,8 +43,8 @@
 //           intersection (S^{-1}(v_k) non-empty). The lane then checks the
 //           masks of the first QUICK roots itself: roots come in rank order,
 //           so these are the largest hubs and they decide most mask tests.
-//           Unpruned (slot, w) pairs and the remaining feasible roots are the
-//           next level's candidates.
+//           Survivors are claimed; freshly claimed (slot, w) pairs and the
+//           remaining feasible roots are the next level's candidates.
 //   test    the rest of the test, one WARP per candidate so that lanes work
 //           in parallel instead of a few lanes looping alone: each lane first
 //           loads its own candidate's label offsets (32 candidates' loads in
@@ -45,8 +52,10 @@
 //           the feasible bit-parallel roots (two each) and compare mask pairs;
 //           if none prunes, they take L(w)'s entries 32 at a time and probe
 //           the root's hash table. Survivors are appended as (w, k, d + 1).
-// The bitmap is cleared once per batch, instead of the per-root lazy reset of
-// Sec. 4.5.1.
+//   clear   after the batch, the lazy reset of Sec. 4.5.1 ("Initialization"):
+//           the only bits set are those of the roots and of the recorded
+//           candidates, so their words are zeroed and nothing else is touched
+//           (instead of clearing B * n / 8 bytes per batch).
 //
 // Level boundaries live in a device descriptor advanced by a one-thread
 // kernel, so the host enqueues several levels ahead and reads back only to
@@ -101,7 +110,7 @@ __global__ void k_batch_init(BatchArgs a) {
             const unsigned long long pos = atomicAdd(&a.ctr->out_n, 1ull);
             if (pos < a.out_cap) a.out[pos] = pack_tuple(k, k, 0);
             else atomicOr(&a.ctr->err, ERR_BUF);
-            atomicOr(&a.visited[(size_t)k * a.W + (slot >> 5)], 1u << (slot & 31));
+            atomicOr(&a.visited[(size_t)slot * a.NW + (k >> 5)], 1u << (k & 31));
         }
         // feasibility masks over the bit-parallel roots
         uint64_t h1 = 0, h01 = 0;
@@ -228,7 +237,7 @@ __device__ __forceinline__ bool quick_masks(const BatchArgs &a, uint32_t k, uint
 
 // entries [lvl_b, lvl_e) of the current level -> candidates of the next
 // 1280 threads per SM (48 registers a thread): the sweep is bound by the
-// latency of its claims and row loads, so resident warps pay: at 72 registers
+// latency of its row loads and claims, so resident warps pay: at 72 registers
 // (768 threads) it ran 14% slower than here. The root's distance row, the same
 // for every lane of a warp, sits once per warp in shared memory.
 template <int BLOCK>
@@ -238,13 +247,13 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
     const uint32_t level = a.desc->level;
-    uint32_t nexp = 0, nclaim = 0;
+    uint32_t nexp = 0, nreach = 0;
     for (unsigned long long j = b + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < e; j += warps) {
         const uint64_t key = a.out[j];
         const uint32_t u = (uint32_t)(key >> 32);
         const uint32_t k = entry_hub((uint32_t)key);
         const uint32_t slot = k - a.k0;
-        const uint32_t sw = slot >> 5, sbit = 1u << (slot & 31);
+        uint32_t *vrow = a.visited + (size_t)slot * a.NW;  // this root's visited set
         // the root's distance row, one copy per warp
         uint4 (&kr)[PLL_MAX_T / 16] = s_kr[threadIdx.x >> 5];
         __syncwarp();  // the previous entry's tests are done with it
@@ -261,23 +270,24 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
             uint64_t c1 = 0, c2 = 0;
             if (x + lane < ee) {
                 w = a.rcol[x + lane];
-                uint32_t *word = &a.visited[(size_t)w * a.W + sw];
+                uint32_t *word = vrow + (w >> 5);
+                const uint32_t wbit = 1u << (w & 31);
                 // w's distance row is requested together with the visited word
-                // (it is read-only), so a fresh claim does not wait for it after
-                // the atomic; rows of vertices already visited are fetched in vain
+                // (it is read-only), so the test does not wait for it after the
+                // lookup; rows of vertices already visited are fetched in vain
                 uint4 wq[PLL_MAX_T / 16];
 #pragma unroll
                 for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
                     wq[c] = (c < (a.tp >> 4))
                                 ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
                                 : make_uint4(0, 0, 0, 0);
-                bool fresh = false;
-                if (!(*(volatile uint32_t *)word & sbit)) fresh = !(atomicOr(word, sbit) & sbit);
-                if (fresh) {
-                    ++nclaim;
+                // a stale word only costs a test: the atomicOr decides the claim
+                if (!(*word & wbit)) {
+                    ++nreach;
                     if (level + 1 >= INF8) atomicOr(&a.ctr->err, ERR_DEPTH);
-                    else keep = !bp_distance_test(a, kr, wq, k, slot, w, level + 1, c1, c2) &&
-                                !quick_masks(a, k, w, c1, c2);
+                    else if (!bp_distance_test(a, kr, wq, k, slot, w, level + 1, c1, c2) &&
+                             !quick_masks(a, k, w, c1, c2))
+                        keep = !(atomicOr(word, wbit) & wbit);
                 }
             }
             if (__any_sync(FULL, keep)) {
@@ -295,8 +305,22 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
     }
     if (lane == 0 && nexp) atomicAdd(&a.ctr->work[2], (unsigned long long)nexp);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nclaim += __shfl_xor_sync(FULL, nclaim, o);
-    if (lane == 0 && nclaim) atomicAdd(&a.ctr->work[3], (unsigned long long)nclaim);
+    for (int o = 16; o > 0; o >>= 1) nreach += __shfl_xor_sync(FULL, nreach, o);
+    if (lane == 0 && nreach) atomicAdd(&a.ctr->work[3], (unsigned long long)nreach);
+}
+
+// Lazy reset: zero the visited words of the batch's roots and candidates (the
+// only bits the batch set; several candidates may share a word)
+__global__ void k_batch_clear(BatchArgs a) {
+    const unsigned long long cn = a.ctr->cand_n < a.cand_cap ? a.ctr->cand_n : a.cand_cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (unsigned long long i = i0; i < a.B; i += stride)
+        a.visited[i * a.NW + ((a.k0 + (uint32_t)i) >> 5)] = 0;
+    for (unsigned long long i = i0; i < cn; i += stride) {
+        const uint64_t c = a.cand[i];
+        a.visited[(c >> 32) * a.NW + ((uint32_t)c >> 5)] = 0;
+    }
 }
 
 // One warp finishes the prune test of one candidate: lanes take the
@@ -496,6 +520,12 @@ static void level_sweeps(const BatchArgs &a, const int *grid, cudaStream_t s, cu
     k_batch_test<BLOCK><<<grid[1], BLOCK, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     k_batch_advance<<<1, 1, 0, s>>>(a, 2);
+}
+
+int batch_clear(const BatchArgs &a, int grid, cudaStream_t s) {
+    k_batch_clear<<<grid > 0 ? grid : 1, 256, 0, s>>>(a);
+    PLL_TRY(cudaGetLastError());
+    return PLL_OK;
 }
 
 // ev: null, or four events recorded around the expand and test sweeps

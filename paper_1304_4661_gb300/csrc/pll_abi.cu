@@ -111,7 +111,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     st.off = m_off.as<uint64_t>();
     st.len = m_len.as<uint32_t>();
     st.cap = m_cap.as<uint32_t>();
-    st.pool_cap = std::max<uint64_t>((uint64_t)n * 16, 1ull << 22);
+    st.pool_cap = test_caps().pool ? test_caps().pool : std::max<uint64_t>((uint64_t)n * 16, 1ull << 22);
     PLL_CHECK(m_pool.alloc(st.pool_cap * 4));
     st.pool = m_pool.as<uint32_t>();
     m_pool.release();  // owned through st.pool from here on (regrow swaps it)
@@ -123,17 +123,21 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
 
     int grid[2] = {0, 0};
     PLL_CHECK(batch_grid(block, grid));
-    const uint32_t wmax = (bmax + 31) / 32;
+    // visited bitmap, one row of ceil(n / 32) words per root slot; cleared once
+    // here, then lazily after each batch (only the words the batch set)
+    const uint32_t NW = (n + 31) / 32;
     DevMem m_vis, m_ht, m_htoff, m_itemp, m_bits, m_cand, m_candc, m_out, m_sorted, m_keep, m_temp;
-    PLL_CHECK(m_vis.alloc((size_t)n * wmax * 4));
-    uint64_t ht_cap = std::max<uint64_t>((uint64_t)bmax * 128, 1ull << 20);
+    PLL_CHECK(m_vis.alloc((size_t)bmax * NW * 4));
+    PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)bmax * NW * 4, s));
+    const TestCaps caps = test_caps();
+    uint64_t ht_cap = caps.ht ? caps.ht : std::max<uint64_t>((uint64_t)bmax * 128, 1ull << 20);
     PLL_CHECK(m_ht.alloc(ht_cap * 4));
     PLL_CHECK(m_htoff.alloc(((size_t)bmax + 1) * 8));
     const size_t itemp_bytes = ((batch_init_temp_bytes(bmax) + 255) & ~(size_t)255) + ((size_t)bmax + 1) * 8 + 256;
     PLL_CHECK(m_itemp.alloc(itemp_bytes));
     PLL_CHECK(m_bits.alloc((size_t)bmax * 16));
-    uint64_t cand_cap = std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
-    uint64_t out_cap = std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
+    uint64_t cand_cap = caps.cand ? caps.cand : std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
+    uint64_t out_cap = caps.out ? caps.out : std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
     size_t temp_bytes = 0;
     const int end_bit = 32 + std::max(1, bit_length(n - 1));
     auto alloc_out = [&]() -> int {
@@ -189,8 +193,9 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     unsigned long long work0[4] = {0, 0, 0, 0};
     while (k0 < n) {
         const uint32_t k1 = (uint32_t)std::min<uint64_t>(n, (uint64_t)k0 + B);
-        // grow the buffers ahead of demand (the last batch scaled to this size)
-        {
+        // grow the buffers ahead of demand (the last batch scaled to this size;
+        // not under the test capacities, which exist to make batches overflow)
+        if (!caps.cand && !caps.out) {
             const double f = 1.5 * (double)(k1 - k0) / (double)last_B;
             if ((double)last_cand * f > (double)cand_cap) {
                 cand_cap = (uint64_t)((double)last_cand * f);
@@ -207,7 +212,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         a.roff = roff; a.rcol = rcol;
         a.bp_d = ix->d_bp_d; a.bp_m = ix->d_bp_m; a.inX = inX;
         a.lab_off = st.off; a.lab_len = st.len; a.pool = st.pool;
-        a.k0 = k0; a.B = k1 - k0; a.W = (a.B + 31) / 32;
+        a.k0 = k0; a.B = k1 - k0; a.NW = NW;
         a.visited = m_vis.as<uint32_t>();
         a.ht = m_ht.as<uint32_t>();
         a.ht_off = m_htoff.as<unsigned long long>();
@@ -217,7 +222,6 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         a.out = m_out.as<uint64_t>(); a.out_cap = out_cap;
         a.ctr = d_ctr; a.desc = d_desc;
         PLL_TRY(cudaEventRecord(ev0, s));
-        PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)n * a.W * 4, s));
         PLL_TRY(cudaMemsetAsync(d_ctr, 0, 16, s));  // cand_n, out_n
         PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
         PLL_CHECK(batch_init(a, m_itemp.p, itemp_bytes, s));
@@ -243,6 +247,14 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             if ((h->c.err & (ERR_DEPTH | ERR_BUF)) || h->d.lvl_b == h->d.lvl_e) break;
             ahead = 2;
         }
+        // lazy reset of the visited rows; an overflowed batch did not record all
+        // of its candidates, so its rows are cleared whole before the redo
+        if (h->c.err & ERR_BUF) {
+            PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)a.B * NW * 4, s));
+        } else {
+            PLL_CHECK(batch_clear(a, grid[0], s));
+            ix->stats.launches += 1;
+        }
         PLL_TRY(cudaEventRecord(ev1, s));
         PLL_CHECK(read_back());
         {
@@ -258,11 +270,15 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             PLL_TRY(cudaMemcpyAsync(&need, m_htoff.as<unsigned long long>() + a.B, 8,
                                     cudaMemcpyDeviceToHost, s));
             PLL_TRY(cudaStreamSynchronize(s));
-            ht_cap = std::max<uint64_t>(need + need / 4, ht_cap * 2);
-            PLL_CHECK(m_ht.alloc(ht_cap * 4));
+            ix->stats.table_fallbacks += 1;
+            if (!caps.ht) {  // the test capacity keeps the pool small for the whole build
+                ht_cap = std::max<uint64_t>(need + need / 4, ht_cap * 2);
+                PLL_CHECK(m_ht.alloc(ht_cap * 4));
+            }
             h->c.err &= ~ERR_TABLE;
         }
         if (h->c.err & ERR_BUF) {  // a buffer overflowed: grow and redo the batch
+            ix->stats.redone_batches += 1;
             PLL_TRY(cudaMemcpyAsync(d_ctr->work, work0, sizeof(work0), cudaMemcpyHostToDevice, s));
             if (h->c.cand_n > cand_cap) {
                 cand_cap = std::max<uint64_t>(cand_cap * 2, h->c.cand_n + h->c.cand_n / 4);
@@ -287,6 +303,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             if (need > st.pool_cap) {
                 uint64_t nc = std::max<uint64_t>(st.pool_cap * 2, 3 * (total + P) + 12 * P);
                 PLL_CHECK(labels_regrow(st, nc, s));
+                ix->stats.pool_regrows += 1;
                 ix->stats.launches += 3;
                 ix->stats.cub_calls += 1;
             }
@@ -533,6 +550,18 @@ bool alloc_should_fail() {
 }
 
 void alloc_note(long long delta) { g_live.fetch_add(delta, std::memory_order_relaxed); }
+
+// test capacities of the pruned stage (0 = the library's own sizing)
+static std::atomic<uint64_t> g_cap_cand{0}, g_cap_out{0}, g_cap_pool{0}, g_cap_ht{0};
+
+TestCaps test_caps() {
+    TestCaps c;
+    c.cand = g_cap_cand.load(std::memory_order_relaxed);
+    c.out = g_cap_out.load(std::memory_order_relaxed);
+    c.pool = g_cap_pool.load(std::memory_order_relaxed);
+    c.ht = g_cap_ht.load(std::memory_order_relaxed);
+    return c;
+}
 
 }  // namespace pll
 
@@ -783,5 +812,12 @@ PLL_API void pll_free(pll_index *idx) { free_index(idx); }
 PLL_API void pll_test_fail_alloc(int64_t k) { g_fail_after.store(k < 0 ? -1 : k); }
 
 PLL_API int64_t pll_test_live_allocs(void) { return g_live.load(); }
+
+PLL_API void pll_test_capacities(uint64_t cand, uint64_t out, uint64_t pool, uint64_t tables) {
+    g_cap_cand.store(cand);
+    g_cap_out.store(out);
+    g_cap_pool.store(pool);
+    g_cap_ht.store(tables);
+}
 
 }  // extern "C"

@@ -96,6 +96,12 @@ void index_release(pll_index *ix);  // frees every device array and the index
 // hook (pll_test_fail_alloc), both kept in pll_abi.cu.
 bool alloc_should_fail();
 void alloc_note(long long delta);
+// initial capacities of the pruned stage's buffers set by pll_test_capacities
+// (0 = the library's own sizing); entries of each buffer
+struct TestCaps {
+    uint64_t cand = 0, out = 0, pool = 0, ht = 0;
+};
+TestCaps test_caps();
 template <class T> inline cudaError_t dev_malloc(T **p, size_t b) {
     *p = nullptr;
     if (alloc_should_fail()) return cudaErrorMemoryAllocation;
@@ -228,8 +234,9 @@ struct BatchArgs {
     const uint64_t *lab_off;   // per-vertex start in pool
     const uint32_t *lab_len;   // per-vertex length (entries with hub < k0)
     const uint32_t *pool;
-    uint32_t k0, B, W;         // roots [k0, k0 + B), W = ceil(B / 32)
-    uint32_t *visited;         // [n][W] bitmap, one bit per batch root
+    uint32_t k0, B, NW;        // roots [k0, k0 + B), NW = ceil(n / 32)
+    uint32_t *visited;         // [B][NW] bitmap: row of root slot s holds one bit
+                               // per vertex (the per-root visited set of Alg. 1)
     uint32_t *ht;              // pool of root label hash tables
     unsigned long long *ht_off;  // [B + 1] table offsets in the pool (exclusive sums)
     unsigned long long ht_cap;   // pool capacity (entries)
@@ -247,6 +254,9 @@ int batch_init(const BatchArgs &a, void *temp, size_t temp_bytes, cudaStream_t s
 size_t batch_init_temp_bytes(uint32_t bmax);
 int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s,
                 cudaEvent_t *ev);
+// lazy reset of the visited bitmap after a batch: clears the words of the
+// roots and of every recorded candidate (all bits the batch set)
+int batch_clear(const BatchArgs &a, int grid, cudaStream_t s);
 
 // k_labels.cu
 struct LabelStore {

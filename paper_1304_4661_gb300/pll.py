@@ -31,7 +31,7 @@ SYMBOLS = [
     "pll_features", "pll_hub_counts", "pll_order_from_scores", "pll_mlp_create", "pll_mlp_free",
     "pll_mlp_set_params", "pll_mlp_get_params", "pll_mlp_forward", "pll_mlp_grad",
     "pll_mlp_read_grad", "pll_mlp_adam", "pll_mlp_train_step", "pll_learned_order",
-    "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs",
+    "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs", "pll_test_capacities",
     "pll_paths_create", "pll_paths_parents", "pll_path_offsets", "pll_path_query",
     "pll_paths_free",
     "pll_build_directed", "pll_dquery", "pll_dlabel_entries", "pll_dexport_labels",
@@ -57,7 +57,9 @@ class Stats(C.Structure):
                 ("launches", C.c_uint64), ("cub_calls", C.c_uint64),
                 ("ms_expand", C.c_double), ("ms_test", C.c_double),
                 ("expand_launches", C.c_uint64), ("test_launches", C.c_uint64),
-                ("candidates", C.c_uint64), ("graphs", C.c_uint32), ("reserved32", C.c_uint32)]
+                ("candidates", C.c_uint64), ("graphs", C.c_uint32), ("reserved32", C.c_uint32),
+                ("redone_batches", C.c_uint64), ("pool_regrows", C.c_uint64),
+                ("table_fallbacks", C.c_uint64)]
 
 
 class ServerOpts(C.Structure):
@@ -192,6 +194,8 @@ def load(build_if_missing: bool = True):
     lib.pll_test_fail_alloc.argtypes = [C.c_int64]
     lib.pll_test_live_allocs.restype = C.c_int64
     lib.pll_test_live_allocs.argtypes = []
+    lib.pll_test_capacities.restype = None
+    lib.pll_test_capacities.argtypes = [C.c_uint64] * 4
     _lib = lib
     return lib
 

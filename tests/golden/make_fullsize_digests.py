@@ -94,6 +94,9 @@ def digest(name: str) -> dict:
         "label_blocks": label_block_digests(L.offsets, L.hubs, L.dists, g.n),
         "pairs": {"count": q, "seed": pseed, "answers": sha(ans),
                   "histogram": {str(i): int(c) for i, c in enumerate(hist) if c}},
+        # work of the sequential pruned BFSs (Alg. 1): vertices dequeued, vertices
+        # labelled, label entries scanned by prune tests, arcs of labelled vertices
+        "sequential_work": ix.counters(),
         "oracle_seconds": {"build": round(t_build, 1), "queries": round(t_query, 1)},
     }
 

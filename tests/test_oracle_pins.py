@@ -316,6 +316,37 @@ def test_tree_centroid_order_label_bound(g):
     assert np.array_equal(ix.query_batch(s, u).reshape(g.n, g.n).astype(np.int64), D)
 
 
+def test_finite_distance_beyond_255_is_a_range_error():
+    """Distances are 8-bit with 255 = unreachable (Sec. 4.5.1, "Arrays"), so a
+    finite distance of 255 or more cannot be answered: Query reports E_RANGE
+    for that pair (reading 10). A 400-vertex path with a centroid order keeps
+    every pruned BFS below depth 255 (the first root's reaches depth 200 and
+    later BFSs stop at earlier hubs), so the index builds, yet its ends are
+    399 apart. Every pair is checked against library APSP: exact below 255,
+    E_RANGE from 255 up. With two bit-parallel roots the second root's
+    unpruned BFS (Sec. 5.2) runs the whole path and the build is E_RANGE."""
+    g = graphs.path(400)
+    order = centroid_order(g)
+    D = brute.apsp(g.offsets, g.cols)
+    assert D.max() == 399 and (D >= 255).sum() > 0
+    for t in (0, 1):
+        ix = oracle.Index(g.offsets, g.cols, t, order=order)
+        far = 0
+        for s in range(g.n):
+            for u in range(g.n):
+                if D[s, u] < 255:
+                    assert ix.query(s, u) == D[s, u], (t, s, u)
+                else:
+                    far += 1
+                    with pytest.raises(oracle.OracleError) as e:
+                        ix.query(s, u)
+                    assert e.value.code == oracle.E_RANGE, (t, s, u)
+        assert far == int((D >= 255).sum())
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.Index(g.offsets, g.cols, 2, order=order)
+    assert e.value.code == oracle.E_RANGE
+
+
 def test_disconnected_and_isolated():
     g = graphs.disjoint(graphs.complete(4), graphs.path(3), graphs.complete(1))
     for t in (0, 2):
