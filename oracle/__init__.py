@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (plain -O2; no vector intrinsics)."""
     if force or not SO.exists() or SO.stat().st_mtime < SRC.stat().st_mtime:
         tmp = SO.with_suffix(f".so.tmp{os.getpid()}")
-        r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", str(tmp), str(SRC)],
+        r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", str(tmp),
+                            str(SRC)],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
@@ -66,6 +67,8 @@ def _load():
         lib.orc_query.argtypes = [vp, u32, u32]
         lib.orc_query_batch.restype = i32
         lib.orc_query_batch.argtypes = [vp, u64, vp, vp, vp]
+        lib.orc_query_batch_mt.restype = i32
+        lib.orc_query_batch_mt.argtypes = [vp, u64, vp, vp, vp, u32]
         lib.orc_total_entries.restype = u64
         lib.orc_total_entries.argtypes = [vp]
         lib.orc_export_labels.restype = None
@@ -190,6 +193,16 @@ class Index:
         st = _load().orc_query_batch(self._h, s.shape[0], s.ctypes.data, u.ctypes.data, out.ctypes.data)
         if st:
             raise OracleError(st, "query_batch")
+        return out[: s.shape[0]]
+
+    def query_batch_mt(self, s, u, threads: int) -> np.ndarray:
+        """query_batch with the pairs split over `threads` host threads."""
+        s, u = _u32(s), _u32(u)
+        out = np.empty(max(s.shape[0], 1), dtype=np.uint8)
+        st = _load().orc_query_batch_mt(self._h, s.shape[0], s.ctypes.data, u.ctypes.data,
+                                        out.ctypes.data, threads)
+        if st:
+            raise OracleError(st, "query_batch_mt")
         return out[: s.shape[0]]
 
     def labels(self) -> Labels:

@@ -19,6 +19,9 @@
  *                         "Sorting Labels"), so they are sorted by construction.
  *   orc_query          -- Query(s, t, L) of Sec. 3.3 (merge join over sorted
  *                         labels) combined with the bit-parallel query.
+ *   orc_query_batch_mt -- the same answers for many pairs, split over POSIX
+ *                         threads (a timing aid for the all-core query rate;
+ *                         every pair still goes through orc_query).
  *   orc_bfs            -- plain BFS distances (ground truth for queries).
  *   orc_label_of       -- the label L(u) that the method must produce for a
  *                         fixed order, computed directly from its closed form:
@@ -68,6 +71,7 @@
  *   - Stored S^0_r(v) is the set of Sec. 5.1 (difference exactly 0), i.e. the
  *     Alg. 3 result with the members of S^{-1}_r(v) removed.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -444,6 +448,55 @@ int orc_query_batch(const orc_index *ix, uint64_t q, const uint32_t *s, const ui
         int d = orc_query(ix, s[x], u[x]);
         if (d < 0) { st = -d; out[x] = INF8; } else out[x] = (uint8_t)d;
     }
+    return st;
+}
+
+/* The same answers as orc_query_batch, with the pairs split into `threads`
+ * contiguous ranges, one POSIX thread each (a timing aid only: each pair is
+ * still answered by orc_query, which reads the index and writes nothing). */
+typedef struct {
+    const orc_index *ix;
+    const uint32_t *s, *u;
+    uint8_t *out;
+    uint64_t lo, hi;
+    int st;
+} orc_qrange;
+
+static void *orc_qrange_run(void *p) {
+    orc_qrange *r = (orc_qrange *)p;
+    r->st = orc_query_batch(r->ix, r->hi - r->lo, r->s + r->lo, r->u + r->lo, r->out + r->lo);
+    return NULL;
+}
+
+int orc_query_batch_mt(const orc_index *ix, uint64_t q, const uint32_t *s, const uint32_t *u,
+                       uint8_t *out, uint32_t threads) {
+    if (threads < 1) threads = 1;
+    if (threads > 1024) threads = 1024;
+    if ((uint64_t)threads > q) threads = q ? (uint32_t)q : 1;
+    orc_qrange *rs = (orc_qrange *)calloc(threads, sizeof(orc_qrange));
+    pthread_t *th = (pthread_t *)calloc(threads, sizeof(pthread_t));
+    if (!rs || !th) { free(rs); free(th); return ORC_E_NOMEM; }
+    for (uint32_t i = 0; i < threads; ++i) {
+        rs[i].ix = ix; rs[i].s = s; rs[i].u = u; rs[i].out = out;
+        rs[i].lo = q * i / threads;
+        rs[i].hi = q * (i + 1) / threads;
+    }
+    uint32_t started = 0;
+    for (uint32_t i = 1; i < threads; ++i, ++started)
+        if (pthread_create(&th[i], NULL, orc_qrange_run, &rs[i]) != 0) break;
+    orc_qrange_run(&rs[0]);
+    int st = rs[0].st;
+    for (uint32_t i = 1; i <= started; ++i) {
+        pthread_join(th[i], NULL);
+        if (rs[i].st && !st) st = rs[i].st;
+    }
+    /* ranges whose thread could not start run here */
+    for (uint32_t i = started + 1; i < threads; ++i) {
+        orc_qrange_run(&rs[i]);
+        if (rs[i].st && !st) st = rs[i].st;
+    }
+    free(rs);
+    free(th);
     return st;
 }
 

@@ -414,3 +414,15 @@ def test_depth_range_error():
     with pytest.raises(oracle.OracleError) as e:
         oracle.Index(g.offsets, g.cols, 0)
     assert e.value.code == oracle.E_RANGE
+
+
+def test_threaded_batch_query_equals_the_plain_one():
+    """orc_query_batch_mt (a timing aid for the all-core query rate) answers
+    exactly as the single-threaded batch query, for any thread count."""
+    g = gg.rmat(12, 16, seed=4)
+    ix = oracle.Index(g.offsets, g.cols, 16)
+    s, u = gg.pairs(g.n, 30_001, 9)
+    ref = ix.query_batch(s, u)
+    for th in (1, 3, 8, 64):
+        assert np.array_equal(ix.query_batch_mt(s, u, th), ref)
+    assert ix.query_batch_mt(s[:2], u[:2], 16).tolist() == ref[:2].tolist()

@@ -15,6 +15,7 @@ stopping at its first failure has already run the tests before it; it passes
 alone and after the others.
 """
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -64,18 +65,25 @@ def test_noalloc_matches_pll_build_twice(make, t):
         cnt = torch.zeros(t, dtype=torch.int32, device="cuda")
         S = torch.zeros(t * 64, dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
-        live, held = lib.pll_test_live_allocs(), torch.cuda.memory_allocated()
-        if call == 1:
-            # the second call runs with every allocation of the library set to
-            # fail: it must still succeed, since it allocates nothing
-            lib.pll_test_fail_alloc(0)
+        # indices left by earlier tests are freed by the garbage collector,
+        # which would move the counts in the middle of the measurement
+        gc.collect()
+        gc.disable()
         try:
-            pll.bp_labels_noalloc(droff, drcol, t, d, masks, roots, cnt, S)
-            torch.cuda.synchronize()
+            live, held = lib.pll_test_live_allocs(), torch.cuda.memory_allocated()
+            if call == 1:
+                # the second call runs with every allocation of the library set
+                # to fail: it must still succeed, since it allocates nothing
+                lib.pll_test_fail_alloc(0)
+            try:
+                pll.bp_labels_noalloc(droff, drcol, t, d, masks, roots, cnt, S)
+                torch.cuda.synchronize()
+            finally:
+                lib.pll_test_fail_alloc(-1)
+            assert lib.pll_test_live_allocs() == live, call
+            assert torch.cuda.memory_allocated() == held, call
         finally:
-            lib.pll_test_fail_alloc(-1)
-        assert lib.pll_test_live_allocs() == live, call
-        assert torch.cuda.memory_allocated() == held, call
+            gc.enable()
         hd = d.cpu().numpy().reshape(n, tp)
         hm = masks.cpu().numpy().view(np.uint64).reshape(n, t, 2)
         assert (hd[:, t:] == 255).all(), call
