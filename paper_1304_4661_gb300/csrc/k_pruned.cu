@@ -83,12 +83,6 @@ __device__ __forceinline__ uint32_t ht_slot(uint32_t h, uint32_t mask) {
     return x >> (32 - lg);
 }
 
-// bytes 0x00/0xff -> 4 bits
-__device__ __forceinline__ uint32_t byte_bits(uint32_t x) {
-    const uint32_t m = x & 0x80808080u;
-    return ((m >> 7) | (m >> 14) | (m >> 21) | (m >> 28)) & 0xfu;
-}
-
 // warp-aggregated append: returns this lane's slot (valid where want is true)
 __device__ __forceinline__ unsigned long long warp_append(unsigned long long *counter, bool want,
                                                           int lane) {
@@ -163,49 +157,67 @@ __global__ void k_ht_sizes(BatchArgs a, unsigned long long *sizes) {
     }
 }
 
-// Cheap part of the prune test, one thread: bit-parallel distances only.
-// Returns true if some d~_i <= level; else fills c1 / c2 with the roots whose
-// masks could still bring d~_i - reduction down to level.
-// wq: w's distance row, loaded by the caller (rows are tp bytes, tp <= 64)
-__device__ __forceinline__ bool bp_distance_test(const BatchArgs &a, const uint4 (&kr)[PLL_MAX_T / 16],
-                                                 const uint4 (&wq)[PLL_MAX_T / 16],
-                                                 uint32_t k, uint32_t slot, uint32_t w,
-                                                 uint32_t level, uint64_t &c1, uint64_t &c2) {
-    c1 = c2 = 0;
-    if (a.t == 0) return false;
-    const uint8_t *dw = a.bp_d + (size_t)w * a.tp;
-    if (level + 2 < INF8) {
-        const uint32_t lv = level * 0x01010101u;
-        const uint32_t l1 = (level + 1) * 0x01010101u, l2 = (level + 2) * 0x01010101u;
+// Cheap part of the prune test, one thread: bit-parallel distances only. With
+// d~_i = d(v_k, r_i) + d(r_i, w), some d~_i <= level prunes (Sec. 5.3: the
+// distance through {r_i} U S_{r_i} is at most d~_i); roots with d~_i = level + 1
+// or level + 2 may still prune through their masks. kr and wq are the rows of
+// v_k and w (nq 16-byte chunks, four roots per 32-bit word); the byte sums
+// saturate at 255, so this form needs level + 2 < 255.
+
+// Phase 1: is some d~_i <= level? Two byte instructions per four roots.
+__device__ __forceinline__ bool bp_prunes(const uint4 *kr, const uint4 (&wq)[PLL_MAX_T / 16], uint32_t nq,
+                                          uint32_t lv) {
+    uint32_t m = 0;
 #pragma unroll
-        for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
-            if (c < (a.tp >> 4)) {
-                const uint4 q = wq[c];
-                const uint4 r = kr[c];
-                const uint32_t wu[4] = {q.x, q.y, q.z, q.w}, wr[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t s = __vaddus4(wu[j], wr[j]);  // 255 saturates
-                    if (__vcmpleu4(s, lv)) return true;
-                    const int sh = 16 * c + 4 * j;
-                    c1 |= (uint64_t)byte_bits(__vcmpeq4(s, l1)) << sh;
-                    c2 |= (uint64_t)byte_bits(__vcmpeq4(s, l2)) << sh;
-                }
-            }
-        }
-    } else {  // depths near 255: plain loop (sums may exceed a byte)
-        const uint8_t *dk = a.bp_d + (size_t)k * a.tp;
-        for (uint32_t i = 0; i < a.t; ++i) {
-            const uint32_t x = dw[i], y = dk[i];
-            if (x == INF8 || y == INF8) continue;
-            const uint32_t td = x + y;
-            if (td <= level) return true;
-            if (td == level + 1) c1 |= 1ull << i;
-            if (td == level + 2) c2 |= 1ull << i;
+    for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
+        if (c < nq) {
+            const uint4 r = kr[c], q = wq[c];
+            m |= __vcmpleu4(__vaddus4(q.x, r.x), lv) | __vcmpleu4(__vaddus4(q.y, r.y), lv) |
+                 __vcmpleu4(__vaddus4(q.z, r.z), lv) | __vcmpleu4(__vaddus4(q.w, r.w), lv);
         }
     }
-    c1 &= a.rootbits[2 * slot + 1];
-    c2 &= a.rootbits[2 * slot];
+    return m != 0;
+}
+
+// bytes 0x00 / 0xff of x -> bits 0..3 (the four 0/1 bits gathered by one multiply)
+__device__ __forceinline__ uint32_t byte_lanes(uint32_t x) { return ((x & 0x01010101u) * 0x01020408u) >> 24; }
+
+// Phase 2, after phase 1 found no prune: c1 = roots with d~_i = level + 1,
+// c2 = roots with d~_i = level + 2.
+__device__ __forceinline__ void bp_feasible(const uint4 *kr, const uint4 (&wq)[PLL_MAX_T / 16], uint32_t nq,
+                                            uint32_t level, uint64_t &c1, uint64_t &c2) {
+    const uint32_t l1 = (level + 1) * 0x01010101u, l2 = (level + 2) * 0x01010101u;
+    c1 = c2 = 0;
+#pragma unroll
+    for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
+        if (c < nq) {
+            const uint4 r = kr[c], q = wq[c];
+            const uint32_t sx = __vaddus4(q.x, r.x), sy = __vaddus4(q.y, r.y);
+            const uint32_t sz = __vaddus4(q.z, r.z), sw = __vaddus4(q.w, r.w);
+            const uint32_t a1 = byte_lanes(__vcmpeq4(sx, l1)) | byte_lanes(__vcmpeq4(sy, l1)) << 4 |
+                                byte_lanes(__vcmpeq4(sz, l1)) << 8 | byte_lanes(__vcmpeq4(sw, l1)) << 12;
+            const uint32_t a2 = byte_lanes(__vcmpeq4(sx, l2)) | byte_lanes(__vcmpeq4(sy, l2)) << 4 |
+                                byte_lanes(__vcmpeq4(sz, l2)) << 8 | byte_lanes(__vcmpeq4(sw, l2)) << 12;
+            c1 |= (uint64_t)a1 << (16 * c);
+            c2 |= (uint64_t)a2 << (16 * c);
+        }
+    }
+}
+
+// The same test for depths near 255, where byte sums would overflow: a plain
+// loop over the roots. Returns true if some d~_i <= level.
+__device__ __noinline__ bool bp_test_plain(const BatchArgs &a, uint32_t k, uint32_t w, uint32_t level,
+                                           uint64_t &c1, uint64_t &c2) {
+    const uint8_t *dw = a.bp_d + (size_t)w * a.tp, *dk = a.bp_d + (size_t)k * a.tp;
+    c1 = c2 = 0;
+    for (uint32_t i = 0; i < a.t; ++i) {
+        const uint32_t x = dw[i], y = dk[i];
+        if (x == INF8 || y == INF8) continue;
+        const uint32_t td = x + y;
+        if (td <= level) return true;
+        if (td == level + 1) c1 |= 1ull << i;
+        if (td == level + 2) c2 |= 1ull << i;
+    }
     return false;
 }
 
@@ -235,42 +247,75 @@ __device__ __forceinline__ bool quick_masks(const BatchArgs &a, uint32_t k, uint
     return p;
 }
 
-// entries [lvl_b, lvl_e) of the current level -> candidates of the next
-// 1280 threads per SM (48 registers a thread): the sweep is bound by the
-// latency of its row loads and claims, so resident warps pay: at 72 registers
-// (768 threads) it ran 14% slower than here. The root's distance row, the same
-// for every lane of a warp, sits once per warp in shared memory.
+// entries [lvl_b, lvl_e) of the current level -> candidates of the next.
+// A warp takes 32 entries at a time and spreads their arcs over its lanes
+// (lane i takes arc base + i of the 32 entries' neighbour lists laid end to
+// end, its entry found by a binary search over a warp scan of the degrees),
+// so the lanes stay busy whatever the degrees: on power-law graphs most
+// labelled vertices have a handful of neighbours, and one warp per entry
+// left over half of its lanes idle. Each entry's root row is staged once in
+// shared memory (64 bytes per entry, BLOCK * 64 bytes per CTA, dynamic).
+// 1280 threads per SM: the sweep hides the latency of its row loads with
+// resident warps.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs a) {
     const int lane = threadIdx.x & 31;
-    __shared__ uint4 s_kr[BLOCK / 32][PLL_MAX_T / 16];
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    extern __shared__ uint4 s_rows[];  // [BLOCK / 32][32][PLL_MAX_T / 16]
+    uint4 *krw = s_rows + (size_t)(threadIdx.x >> 5) * 32 * (PLL_MAX_T / 16);
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
-    const uint32_t level = a.desc->level;
+    const uint32_t level = a.desc->level, nq = a.tp >> 4;
+    const uint32_t nlevel = level + 1;                  // level of the candidates
+    const bool near = nlevel + 2 >= INF8;               // byte sums could overflow
+    const uint32_t lv = nlevel * 0x01010101u;
     uint32_t nexp = 0, nreach = 0;
-    for (unsigned long long j = b + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < e; j += warps) {
-        const uint64_t key = a.out[j];
-        const uint32_t u = (uint32_t)(key >> 32);
-        const uint32_t k = entry_hub((uint32_t)key);
-        const uint32_t slot = k - a.k0;
-        uint32_t *vrow = a.visited + (size_t)slot * a.NW;  // this root's visited set
-        // the root's distance row, one copy per warp
-        uint4 (&kr)[PLL_MAX_T / 16] = s_kr[threadIdx.x >> 5];
-        __syncwarp();  // the previous entry's tests are done with it
-        if (lane < PLL_MAX_T / 16)
-            kr[lane] = ((uint32_t)lane < (a.tp >> 4))
-                           ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp) + lane)
-                           : make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (unsigned long long j0 = b + gw * 32; j0 < e; j0 += nwarps * 32) {
+        const unsigned long long j = j0 + lane;
+        uint32_t k = 0, eb = 0, deg = 0;
+        if (j < e) {
+            const uint64_t key = a.out[j];
+            const uint32_t u = (uint32_t)(key >> 32);
+            k = entry_hub((uint32_t)key);
+            eb = a.roff[u];
+            deg = a.roff[u + 1] - eb;
+        }
+        __syncwarp();  // the previous group's tests are done with the rows
+        if (j < e) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp);
+#pragma unroll
+            for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
+                if (c < nq) krw[lane * (PLL_MAX_T / 16) + c] = __ldg(src + c);
+        }
         __syncwarp();
-        const uint32_t eb = a.roff[u], ee = a.roff[u + 1];
-        nexp += ee - eb;
-        for (uint32_t x = eb; x < ee; x += 32) {
+        // arcs of the 32 entries laid end to end: lane i's entry owns arcs
+        // [excl_i, excl_i + deg_i)
+        uint32_t incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t excl = incl - deg;
+        const uint32_t base_col = eb - excl;  // arc x of the group is rcol[base_col_i + x]
+        nexp += deg;
+        for (uint32_t x0 = 0; x0 < total; x0 += 32) {
+            const uint32_t x = x0 + lane;
+            // owner: the last entry whose first arc is <= x (excl is non-decreasing)
+            uint32_t i = 0;
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(FULL, excl, i + step) <= x) i += step;
+            const uint32_t ki = __shfl_sync(FULL, k, i);
+            const uint32_t ci = __shfl_sync(FULL, base_col, i);
             bool keep = false;
-            uint32_t w = 0;
+            uint32_t w = 0, slot = 0;
             uint64_t c1 = 0, c2 = 0;
-            if (x + lane < ee) {
-                w = a.rcol[x + lane];
-                uint32_t *word = vrow + (w >> 5);
+            if (x < total) {
+                w = a.rcol[ci + x];
+                slot = ki - a.k0;
+                uint32_t *word = a.visited + (size_t)slot * a.NW + (w >> 5);
                 const uint32_t wbit = 1u << (w & 31);
                 // w's distance row is requested together with the visited word
                 // (it is read-only), so the test does not wait for it after the
@@ -278,16 +323,27 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
                 uint4 wq[PLL_MAX_T / 16];
 #pragma unroll
                 for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
-                    wq[c] = (c < (a.tp >> 4))
-                                ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
-                                : make_uint4(0, 0, 0, 0);
+                    wq[c] = (c < nq) ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
+                                     : make_uint4(0, 0, 0, 0);
                 // a stale word only costs a test: the atomicOr decides the claim
                 if (!(*word & wbit)) {
                     ++nreach;
-                    if (level + 1 >= INF8) atomicOr(&a.ctr->err, ERR_DEPTH);
-                    else if (!bp_distance_test(a, kr, wq, k, slot, w, level + 1, c1, c2) &&
-                             !quick_masks(a, k, w, c1, c2))
-                        keep = !(atomicOr(word, wbit) & wbit);
+                    bool pruned;
+                    if (nlevel >= INF8) {
+                        atomicOr(&a.ctr->err, ERR_DEPTH);
+                        pruned = true;
+                    } else if (!near) {
+                        const uint4 *kr = krw + i * (PLL_MAX_T / 16);
+                        pruned = bp_prunes(kr, wq, nq, lv);
+                        if (!pruned) bp_feasible(kr, wq, nq, nlevel, c1, c2);
+                    } else {
+                        pruned = bp_test_plain(a, ki, w, nlevel, c1, c2);
+                    }
+                    if (!pruned) {
+                        c1 &= a.rootbits[2 * slot + 1];
+                        c2 &= a.rootbits[2 * slot];
+                        if (!quick_masks(a, ki, w, c1, c2)) keep = !(atomicOr(word, wbit) & wbit);
+                    }
                 }
             }
             if (__any_sync(FULL, keep)) {
@@ -303,11 +359,17 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
             }
         }
     }
-    if (lane == 0 && nexp) atomicAdd(&a.ctr->work[2], (unsigned long long)nexp);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nreach += __shfl_xor_sync(FULL, nreach, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        nexp += __shfl_xor_sync(FULL, nexp, o);
+        nreach += __shfl_xor_sync(FULL, nreach, o);
+    }
+    if (lane == 0 && nexp) atomicAdd(&a.ctr->work[2], (unsigned long long)nexp);
     if (lane == 0 && nreach) atomicAdd(&a.ctr->work[3], (unsigned long long)nreach);
 }
+
+template <int BLOCK>
+constexpr size_t expand_smem() { return (size_t)BLOCK * (PLL_MAX_T / 16) * sizeof(uint4); }
 
 // Lazy reset: zero the visited words of the batch's roots and candidates (the
 // only bits the batch set; several candidates may share a word)
@@ -464,7 +526,10 @@ __global__ void k_batch_advance(BatchArgs a, int phase) {
 
 template <int BLOCK>
 static cudaError_t occupancy(int *pe, int *pt) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(pe, k_batch_expand<BLOCK>, BLOCK, 0);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_expand<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)expand_smem<BLOCK>());
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(pe, k_batch_expand<BLOCK>, BLOCK, expand_smem<BLOCK>());
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(pt, k_batch_test<BLOCK>, BLOCK, 0);
     return e;
 }
@@ -513,7 +578,7 @@ int batch_init(const BatchArgs &a, void *temp, size_t temp_bytes, cudaStream_t s
 template <int BLOCK>
 static void level_sweeps(const BatchArgs &a, const int *grid, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
-    k_batch_expand<BLOCK><<<grid[0], BLOCK, 0, s>>>(a);
+    k_batch_expand<BLOCK><<<grid[0], BLOCK, expand_smem<BLOCK>(), s>>>(a);
     if (ev) cudaEventRecord(ev[1], s);
     k_batch_advance<<<1, 1, 0, s>>>(a, 1);
     if (ev) cudaEventRecord(ev[2], s);
