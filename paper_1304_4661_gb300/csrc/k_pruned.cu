@@ -164,19 +164,23 @@ __global__ void k_ht_sizes(BatchArgs a, unsigned long long *sizes) {
 // v_k and w (nq 16-byte chunks, four roots per 32-bit word); the byte sums
 // saturate at 255, so this form needs level + 2 < 255.
 
-// Phase 1: is some d~_i <= level? Two byte instructions per four roots.
+// Phase 1: is some d~_i <= level? Two byte instructions per four roots, with
+// an exit at the first word that prunes: roots come in rank order (Sec. 5.4),
+// so the first words, the largest hubs, prune most vertices, and the exit saves
+// a fifth of the sweep's time against testing all t roots first.
 __device__ __forceinline__ bool bp_prunes(const uint4 *kr, const uint4 (&wq)[PLL_MAX_T / 16], uint32_t nq,
                                           uint32_t lv) {
-    uint32_t m = 0;
 #pragma unroll
     for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
         if (c < nq) {
             const uint4 r = kr[c], q = wq[c];
-            m |= __vcmpleu4(__vaddus4(q.x, r.x), lv) | __vcmpleu4(__vaddus4(q.y, r.y), lv) |
-                 __vcmpleu4(__vaddus4(q.z, r.z), lv) | __vcmpleu4(__vaddus4(q.w, r.w), lv);
+            if (__vcmpleu4(__vaddus4(q.x, r.x), lv)) return true;
+            if (__vcmpleu4(__vaddus4(q.y, r.y), lv)) return true;
+            if (__vcmpleu4(__vaddus4(q.z, r.z), lv)) return true;
+            if (__vcmpleu4(__vaddus4(q.w, r.w), lv)) return true;
         }
     }
-    return m != 0;
+    return false;
 }
 
 // bytes 0x00 / 0xff of x -> bits 0..3 (the four 0/1 bits gathered by one multiply)
@@ -247,116 +251,91 @@ __device__ __forceinline__ bool quick_masks(const BatchArgs &a, uint32_t k, uint
     return p;
 }
 
-// entries [lvl_b, lvl_e) of the current level -> candidates of the next.
-// A warp takes 32 entries at a time and spreads their arcs over its lanes
-// (lane i takes arc base + i of the 32 entries' neighbour lists laid end to
-// end, its entry found by a binary search over a warp scan of the degrees),
-// so the lanes stay busy whatever the degrees: on power-law graphs most
-// labelled vertices have a handful of neighbours, and one warp per entry
-// left over half of its lanes idle. Each entry's root row is staged once in
-// shared memory (64 bytes per entry, BLOCK * 64 bytes per CTA, dynamic).
-// 1280 threads per SM: the sweep hides the latency of its row loads with
-// resident warps.
+
+// One arc (u, w) of an entry of root ki (batch slot `slot`; kr = its row in
+// shared memory): look w up in the root's visited row; if unvisited, the
+// bit-parallel test and the first masks; claim w if it survives. Returns true
+// for a fresh claim (w becomes a candidate with feasible roots c1 / c2).
+__device__ __forceinline__ bool expand_arc(const BatchArgs &a, uint32_t ki, uint32_t slot, uint32_t w,
+                                           const uint4 *kr, uint32_t nq, uint32_t nlevel, bool near,
+                                           uint32_t lv, uint64_t &c1, uint64_t &c2, uint32_t &nreach) {
+    uint32_t *word = a.visited + (size_t)slot * a.NW + (w >> 5);
+    const uint32_t wbit = 1u << (w & 31);
+    uint4 wq[PLL_MAX_T / 16];
+#pragma unroll
+    for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
+        wq[c] = (c < nq) ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
+                         : make_uint4(0, 0, 0, 0);
+    if (*word & wbit) return false;
+    ++nreach;
+    bool pruned;
+    if (nlevel >= INF8) {
+        atomicOr(&a.ctr->err, ERR_DEPTH);
+        return false;
+    } else if (!near) {
+        pruned = bp_prunes(kr, wq, nq, lv);
+        if (!pruned) bp_feasible(kr, wq, nq, nlevel, c1, c2);
+    } else {
+        pruned = bp_test_plain(a, ki, w, nlevel, c1, c2);
+    }
+    if (pruned) return false;
+    c1 &= a.rootbits[2 * slot + 1];
+    c2 &= a.rootbits[2 * slot];
+    if (quick_masks(a, ki, w, c1, c2)) return false;
+    return !(atomicOr(word, wbit) & wbit);
+}
+
+__device__ __forceinline__ void append_cand(const BatchArgs &a, bool keep, int lane, uint32_t slot, uint32_t w,
+                                            uint64_t c1, uint64_t c2) {
+    if (__any_sync(FULL, keep)) {
+        const unsigned long long pos = warp_append(&a.ctr->cand_n, keep, lane);
+        if (keep) {
+            if (pos < a.cand_cap) {
+                a.cand[pos] = ((uint64_t)slot << 32) | w;
+                reinterpret_cast<ulonglong2 *>(a.candc)[pos] = make_ulonglong2(c1, c2);
+            } else {
+                atomicOr(&a.ctr->err, ERR_BUF);
+            }
+        }
+    }
+}
+// entries [lvl_b, lvl_e) of the current level -> candidates of the next, one
+// warp per entry, 32 consecutive arcs per step (coalesced column loads; the
+// root's row, the same for every lane, sits once per warp in shared memory).
+// 1280 threads per SM (48 registers a thread): the sweep hides the latency of
+// its row and visited-word loads with resident warps.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs a) {
     const int lane = threadIdx.x & 31;
-    extern __shared__ uint4 s_rows[];  // [BLOCK / 32][32][PLL_MAX_T / 16]
-    uint4 *krw = s_rows + (size_t)(threadIdx.x >> 5) * 32 * (PLL_MAX_T / 16);
+    extern __shared__ uint4 s_rows[];
+    uint4 *kr = s_rows + (size_t)(threadIdx.x >> 5) * (PLL_MAX_T / 16);
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
     const uint32_t level = a.desc->level, nq = a.tp >> 4;
-    const uint32_t nlevel = level + 1;                  // level of the candidates
-    const bool near = nlevel + 2 >= INF8;               // byte sums could overflow
+    const uint32_t nlevel = level + 1;
+    const bool near = nlevel + 2 >= INF8;
     const uint32_t lv = nlevel * 0x01010101u;
     uint32_t nexp = 0, nreach = 0;
-    for (unsigned long long j0 = b + gw * 32; j0 < e; j0 += nwarps * 32) {
-        const unsigned long long j = j0 + lane;
-        uint32_t k = 0, eb = 0, deg = 0;
-        if (j < e) {
-            const uint64_t key = a.out[j];
-            const uint32_t u = (uint32_t)(key >> 32);
-            k = entry_hub((uint32_t)key);
-            eb = a.roff[u];
-            deg = a.roff[u + 1] - eb;
-        }
-        __syncwarp();  // the previous group's tests are done with the rows
-        if (j < e) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp);
-#pragma unroll
-            for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
-                if (c < nq) krw[lane * (PLL_MAX_T / 16) + c] = __ldg(src + c);
-        }
+    for (unsigned long long j = b + gw; j < e; j += nwarps) {
+        const uint64_t key = a.out[j];
+        const uint32_t u = (uint32_t)(key >> 32);
+        const uint32_t k = entry_hub((uint32_t)key);
+        const uint32_t slot = k - a.k0;
         __syncwarp();
-        // arcs of the 32 entries laid end to end: lane i's entry owns arcs
-        // [excl_i, excl_i + deg_i)
-        uint32_t incl = deg;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        const uint32_t excl = incl - deg;
-        const uint32_t base_col = eb - excl;  // arc x of the group is rcol[base_col_i + x]
-        nexp += deg;
-        for (uint32_t x0 = 0; x0 < total; x0 += 32) {
-            const uint32_t x = x0 + lane;
-            // owner: the last entry whose first arc is <= x (excl is non-decreasing)
-            uint32_t i = 0;
-#pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(FULL, excl, i + step) <= x) i += step;
-            const uint32_t ki = __shfl_sync(FULL, k, i);
-            const uint32_t ci = __shfl_sync(FULL, base_col, i);
+        if ((uint32_t)lane < nq) kr[lane] = __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp) + lane);
+        __syncwarp();
+        const uint32_t eb = a.roff[u], ee = a.roff[u + 1];
+        if (lane == 0) nexp += ee - eb;
+        for (uint32_t x = eb; x < ee; x += 32) {
             bool keep = false;
-            uint32_t w = 0, slot = 0;
+            uint32_t w = 0;
             uint64_t c1 = 0, c2 = 0;
-            if (x < total) {
-                w = a.rcol[ci + x];
-                slot = ki - a.k0;
-                uint32_t *word = a.visited + (size_t)slot * a.NW + (w >> 5);
-                const uint32_t wbit = 1u << (w & 31);
-                // w's distance row is requested together with the visited word
-                // (it is read-only), so the test does not wait for it after the
-                // lookup; rows of vertices already visited are fetched in vain
-                uint4 wq[PLL_MAX_T / 16];
-#pragma unroll
-                for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
-                    wq[c] = (c < nq) ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
-                                     : make_uint4(0, 0, 0, 0);
-                // a stale word only costs a test: the atomicOr decides the claim
-                if (!(*word & wbit)) {
-                    ++nreach;
-                    bool pruned;
-                    if (nlevel >= INF8) {
-                        atomicOr(&a.ctr->err, ERR_DEPTH);
-                        pruned = true;
-                    } else if (!near) {
-                        const uint4 *kr = krw + i * (PLL_MAX_T / 16);
-                        pruned = bp_prunes(kr, wq, nq, lv);
-                        if (!pruned) bp_feasible(kr, wq, nq, nlevel, c1, c2);
-                    } else {
-                        pruned = bp_test_plain(a, ki, w, nlevel, c1, c2);
-                    }
-                    if (!pruned) {
-                        c1 &= a.rootbits[2 * slot + 1];
-                        c2 &= a.rootbits[2 * slot];
-                        if (!quick_masks(a, ki, w, c1, c2)) keep = !(atomicOr(word, wbit) & wbit);
-                    }
-                }
+            if (x + lane < ee) {
+                w = a.rcol[x + lane];
+                keep = expand_arc(a, k, slot, w, kr, nq, nlevel, near, lv, c1, c2, nreach);
             }
-            if (__any_sync(FULL, keep)) {
-                const unsigned long long pos = warp_append(&a.ctr->cand_n, keep, lane);
-                if (keep) {
-                    if (pos < a.cand_cap) {
-                        a.cand[pos] = ((uint64_t)slot << 32) | w;
-                        reinterpret_cast<ulonglong2 *>(a.candc)[pos] = make_ulonglong2(c1, c2);
-                    } else {
-                        atomicOr(&a.ctr->err, ERR_BUF);
-                    }
-                }
-            }
+            append_cand(a, keep, lane, slot, w, c1, c2);
         }
     }
 #pragma unroll
@@ -369,7 +348,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
 }
 
 template <int BLOCK>
-constexpr size_t expand_smem() { return (size_t)BLOCK * (PLL_MAX_T / 16) * sizeof(uint4); }
+constexpr size_t expand_smem() { return (size_t)(BLOCK / 32) * (PLL_MAX_T / 16) * sizeof(uint4); }
 
 // Lazy reset: zero the visited words of the batch's roots and candidates (the
 // only bits the batch set; several candidates may share a word)
