@@ -208,6 +208,62 @@ __device__ __forceinline__ void bp_feasible(const uint4 *kr, const uint4 (&wq)[P
     }
 }
 
+// The clamped rows: bp_c holds min(d(r_i, v), 63) for every byte of bp_d
+// (unreachable, 255, also becomes 63). Two clamped bytes add up to at most
+// 126 with no carry between bytes, so plain 32-bit arithmetic tests four roots
+// at once (the byte-SIMD intrinsics above take several instructions each).
+// For a candidate level L <= FAST_LEVEL the test is exact: a clamped byte
+// stands for a distance >= 63 > L + 2, so its sum can neither reach L nor
+// equal L + 1 or L + 2, clamped or not.
+constexpr uint32_t CLAMP = 63;
+constexpr uint32_t FAST_LEVEL = CLAMP - 3;
+
+// Phase 1 on clamped rows: with lb = (0x80 + L) in every byte, the byte of
+// lb - (q + r) keeps its top bit iff q + r <= L (no borrow crosses a byte:
+// every byte of lb is above every byte sum).
+__device__ __forceinline__ bool bp_prunes_c(const uint4 *kr, const uint4 (&wq)[PLL_MAX_T / 16], uint32_t nq,
+                                            uint32_t lb) {
+#pragma unroll
+    for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
+        if (c < nq) {
+            const uint4 r = kr[c], q = wq[c];
+            if ((lb - (q.x + r.x)) & 0x80808080u) return true;
+            if ((lb - (q.y + r.y)) & 0x80808080u) return true;
+            if ((lb - (q.z + r.z)) & 0x80808080u) return true;
+            if ((lb - (q.w + r.w)) & 0x80808080u) return true;
+        }
+    }
+    return false;
+}
+
+// bits 0..3: which bytes of s equal those of cb (every byte of s ^ cb is
+// below 0x80, so (x | 0x80) - 1 keeps its top bit iff the byte x is not 0)
+__device__ __forceinline__ uint32_t eq_lanes(uint32_t s, uint32_t cb) {
+    const uint32_t x = s ^ cb;
+    const uint32_t z = ~((x | 0x80808080u) - 0x01010101u) & 0x80808080u;
+    return ((z >> 7) * 0x01020408u) >> 24;
+}
+
+// Phase 2 on clamped rows: c1 = roots with d~_i = L + 1, c2 = roots with L + 2.
+__device__ __forceinline__ void bp_feasible_c(const uint4 *kr, const uint4 (&wq)[PLL_MAX_T / 16], uint32_t nq,
+                                              uint32_t level, uint64_t &c1, uint64_t &c2) {
+    const uint32_t l1 = (level + 1) * 0x01010101u, l2 = (level + 2) * 0x01010101u;
+    c1 = c2 = 0;
+#pragma unroll
+    for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c) {
+        if (c < nq) {
+            const uint4 r = kr[c], q = wq[c];
+            const uint32_t sx = q.x + r.x, sy = q.y + r.y, sz = q.z + r.z, sw = q.w + r.w;
+            const uint32_t a1 = eq_lanes(sx, l1) | eq_lanes(sy, l1) << 4 | eq_lanes(sz, l1) << 8 |
+                                eq_lanes(sw, l1) << 12;
+            const uint32_t a2 = eq_lanes(sx, l2) | eq_lanes(sy, l2) << 4 | eq_lanes(sz, l2) << 8 |
+                                eq_lanes(sw, l2) << 12;
+            c1 |= (uint64_t)a1 << (16 * c);
+            c2 |= (uint64_t)a2 << (16 * c);
+        }
+    }
+}
+
 // The same test for depths near 255, where byte sums would overflow: a plain
 // loop over the roots. Returns true if some d~_i <= level.
 __device__ __noinline__ bool bp_test_plain(const BatchArgs &a, uint32_t k, uint32_t w, uint32_t level,
@@ -253,18 +309,20 @@ __device__ __forceinline__ bool quick_masks(const BatchArgs &a, uint32_t k, uint
 
 
 // One arc (u, w) of an entry of root ki (batch slot `slot`; kr = its row in
-// shared memory): look w up in the root's visited row; if unvisited, the
-// bit-parallel test and the first masks; claim w if it survives. Returns true
-// for a fresh claim (w becomes a candidate with feasible roots c1 / c2).
-__device__ __forceinline__ bool expand_arc(const BatchArgs &a, uint32_t ki, uint32_t slot, uint32_t w,
-                                           const uint4 *kr, uint32_t nq, uint32_t nlevel, bool near,
-                                           uint32_t lv, uint64_t &c1, uint64_t &c2, uint32_t &nreach) {
+// shared memory, from `rows`): look w up in the root's visited row; if
+// unvisited, the bit-parallel test and the first masks; claim w if it
+// survives. Returns true for a fresh claim (w becomes a candidate with
+// feasible roots c1 / c2). fast: the rows are the clamped ones.
+__device__ __forceinline__ bool expand_arc(const BatchArgs &a, const uint8_t *rows, uint32_t ki, uint32_t slot,
+                                           uint32_t w, const uint4 *kr, uint32_t nq, uint32_t nlevel,
+                                           bool fast, bool near, uint32_t lv, uint64_t &c1, uint64_t &c2,
+                                           uint32_t &nreach) {
     uint32_t *word = a.visited + (size_t)slot * a.NW + (w >> 5);
     const uint32_t wbit = 1u << (w & 31);
     uint4 wq[PLL_MAX_T / 16];
 #pragma unroll
     for (uint32_t c = 0; c < PLL_MAX_T / 16; ++c)
-        wq[c] = (c < nq) ? __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)w * a.tp) + c)
+        wq[c] = (c < nq) ? __ldg(reinterpret_cast<const uint4 *>(rows + (size_t)w * a.tp) + c)
                          : make_uint4(0, 0, 0, 0);
     if (*word & wbit) return false;
     ++nreach;
@@ -272,6 +330,9 @@ __device__ __forceinline__ bool expand_arc(const BatchArgs &a, uint32_t ki, uint
     if (nlevel >= INF8) {
         atomicOr(&a.ctr->err, ERR_DEPTH);
         return false;
+    } else if (fast) {
+        pruned = bp_prunes_c(kr, wq, nq, lv);
+        if (!pruned) bp_feasible_c(kr, wq, nq, nlevel, c1, c2);
     } else if (!near) {
         pruned = bp_prunes(kr, wq, nq, lv);
         if (!pruned) bp_feasible(kr, wq, nq, nlevel, c1, c2);
@@ -313,9 +374,11 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
     const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
     const uint32_t level = a.desc->level, nq = a.tp >> 4;
-    const uint32_t nlevel = level + 1;
-    const bool near = nlevel + 2 >= INF8;
-    const uint32_t lv = nlevel * 0x01010101u;
+    const uint32_t nlevel = level + 1;                // level of the candidates
+    const bool fast = nlevel <= FAST_LEVEL;           // clamped rows, plain arithmetic
+    const bool near = nlevel + 2 >= INF8;             // byte sums could overflow
+    const uint32_t lv = fast ? (0x80u + nlevel) * 0x01010101u : nlevel * 0x01010101u;
+    const uint8_t *rows = fast ? a.bp_c : a.bp_d;
     uint32_t nexp = 0, nreach = 0;
     for (unsigned long long j = b + gw; j < e; j += nwarps) {
         const uint64_t key = a.out[j];
@@ -323,7 +386,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
         const uint32_t k = entry_hub((uint32_t)key);
         const uint32_t slot = k - a.k0;
         __syncwarp();
-        if ((uint32_t)lane < nq) kr[lane] = __ldg(reinterpret_cast<const uint4 *>(a.bp_d + (size_t)k * a.tp) + lane);
+        if ((uint32_t)lane < nq) kr[lane] = __ldg(reinterpret_cast<const uint4 *>(rows + (size_t)k * a.tp) + lane);
         __syncwarp();
         const uint32_t eb = a.roff[u], ee = a.roff[u + 1];
         if (lane == 0) nexp += ee - eb;
@@ -333,7 +396,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
             uint64_t c1 = 0, c2 = 0;
             if (x + lane < ee) {
                 w = a.rcol[x + lane];
-                keep = expand_arc(a, k, slot, w, kr, nq, nlevel, near, lv, c1, c2, nreach);
+                keep = expand_arc(a, rows, k, slot, w, kr, nq, nlevel, fast, near, lv, c1, c2, nreach);
             }
             append_cand(a, keep, lane, slot, w, c1, c2);
         }
@@ -349,6 +412,22 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
 
 template <int BLOCK>
 constexpr size_t expand_smem() { return (size_t)(BLOCK / 32) * (PLL_MAX_T / 16) * sizeof(uint4); }
+
+// bp_c = min(bp_d, CLAMP) bytewise, 16 bytes per thread and step
+__global__ void k_clamp_rows(const uint4 *bp_d, uint4 *bp_c, size_t n16) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x) {
+        uint4 v = bp_d[i];
+        uint32_t *x = reinterpret_cast<uint32_t *>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            // bytes >= 64 have one of their two top bits set: they become 63
+            const uint32_t hi = x[j] & 0xC0C0C0C0u;
+            const uint32_t big = ((hi >> 6) | (hi >> 7)) & 0x01010101u;
+            x[j] = (x[j] & 0x3F3F3F3Fu) | (big * CLAMP);
+        }
+        bp_c[i] = v;
+    }
+}
 
 // Lazy reset: zero the visited words of the batch's roots and candidates (the
 // only bits the batch set; several candidates may share a word)
@@ -564,6 +643,14 @@ static void level_sweeps(const BatchArgs &a, const int *grid, cudaStream_t s, cu
     k_batch_test<BLOCK><<<grid[1], BLOCK, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     k_batch_advance<<<1, 1, 0, s>>>(a, 2);
+}
+
+int batch_clamp_rows(const uint8_t *bp_d, uint8_t *bp_c, size_t bytes, int grid, cudaStream_t s) {
+    if (bytes == 0) return PLL_OK;
+    k_clamp_rows<<<grid > 0 ? grid : 1, 256, 0, s>>>(reinterpret_cast<const uint4 *>(bp_d),
+                                                     reinterpret_cast<uint4 *>(bp_c), bytes / 16);
+    PLL_TRY(cudaGetLastError());
+    return PLL_OK;
 }
 
 int batch_clear(const BatchArgs &a, int grid, cudaStream_t s) {

@@ -123,6 +123,11 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
 
     int grid[2] = {0, 0};
     PLL_CHECK(batch_grid(block, grid));
+    // clamped copy of the bit-parallel distance rows for the expand sweep
+    DevMem m_bpc;
+    PLL_CHECK(m_bpc.alloc(std::max<size_t>((size_t)n * ix->tp, 16)));
+    PLL_CHECK(batch_clamp_rows(ix->d_bp_d, m_bpc.as<uint8_t>(), (size_t)n * ix->tp, grid[0], s));
+    ix->stats.launches += 1;
     // visited bitmap, one row of ceil(n / 32) words per root slot; cleared once
     // here, then lazily after each batch (only the words the batch set)
     const uint32_t NW = (n + 31) / 32;
@@ -210,7 +215,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         BatchArgs a{};
         a.n = n; a.t = ix->t; a.tp = ix->tp;
         a.roff = roff; a.rcol = rcol;
-        a.bp_d = ix->d_bp_d; a.bp_m = ix->d_bp_m; a.inX = inX;
+        a.bp_d = ix->d_bp_d; a.bp_c = m_bpc.as<uint8_t>(); a.bp_m = ix->d_bp_m; a.inX = inX;
         a.lab_off = st.off; a.lab_len = st.len; a.pool = st.pool;
         a.k0 = k0; a.B = k1 - k0; a.NW = NW;
         a.visited = m_vis.as<uint32_t>();

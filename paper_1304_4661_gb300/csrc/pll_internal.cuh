@@ -229,6 +229,7 @@ struct BatchArgs {
     uint32_t n, t, tp;
     const uint32_t *roff, *rcol;
     const uint8_t *bp_d;
+    const uint8_t *bp_c;       // bp_d with every byte clamped to 63 (same stride)
     const uint64_t *bp_m;
     const uint8_t *inX;
     const uint64_t *lab_off;   // per-vertex start in pool
@@ -257,6 +258,8 @@ int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_
 // lazy reset of the visited bitmap after a batch: clears the words of the
 // roots and of every recorded candidate (all bits the batch set)
 int batch_clear(const BatchArgs &a, int grid, cudaStream_t s);
+// bp_c = min(bp_d, 63) bytewise (bytes a multiple of 16)
+int batch_clamp_rows(const uint8_t *bp_d, uint8_t *bp_c, size_t bytes, int grid, cudaStream_t s);
 
 // k_labels.cu
 struct LabelStore {
