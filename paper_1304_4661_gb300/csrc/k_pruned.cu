@@ -94,6 +94,15 @@ __device__ __forceinline__ unsigned long long warp_append(unsigned long long *co
     return base + __popc(m & ((1u << lane) - 1u));
 }
 
+// Bit of hub rank h in a root's 1024-bit filter: the top 10 bits of the same
+// kind of mix as ht_slot (hub ranks of a batch build share their low bits).
+__device__ __forceinline__ uint32_t filt_bit(uint32_t h) {
+    uint32_t x = h * 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    return x >> 22;
+}
+
 __global__ void k_batch_init(BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -123,10 +132,22 @@ __global__ void k_batch_init(BatchArgs a) {
             a.rootbits[2 * slot] = h1;
             a.rootbits[2 * slot + 1] = h01;
         }
+        // a 1024-bit filter of L(v_k)'s hubs: most hubs of a candidate's label
+        // are not in the root's, and the filter tells so with one load
+        const uint32_t len = a.lab_len[k];
+        uint32_t *filt = a.filt + (size_t)slot * FILT_WORDS;
+        filt[lane] = 0;
+        __syncwarp();
+        {
+            const uint32_t *lab = a.pool + a.lab_off[k];
+            for (uint32_t j = lane; j < len; j += 32) {
+                const uint32_t fb = filt_bit(entry_hub(lab[j]));
+                atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+            }
+        }
         // root array T as a hash table of 2 x |L(v_k)| slots (very long labels,
         // and tables past the pool's end, are binary-searched instead; the host
         // grows the pool for the next batches)
-        const uint32_t len = a.lab_len[k];
         const unsigned long long tb = a.ht_off[slot], te = a.ht_off[slot + 1];
         if (te > a.ht_cap) {
             if (lane == 0) atomicOr(&a.ctr->err, ERR_TABLE);
@@ -443,70 +464,32 @@ __global__ void k_batch_clear(BatchArgs a) {
     }
 }
 
-// One warp finishes the prune test of one candidate: lanes take the
-// feasible bit-parallel roots (two each) and compare mask pairs in one round;
-// if none prunes, lanes take L(w)'s entries 32 at a time and probe the root's
-// hash table.
-__device__ __forceinline__ bool prune_warp(const BatchArgs &a, uint32_t slot, uint32_t k, uint32_t w,
-                                           uint32_t level, uint64_t c1, uint64_t c2, uint32_t len,
-                                           uint64_t lab_off, uint32_t rlen, uint64_t rlab_off,
-                                           int lane, uint32_t &n_scan, uint32_t &n_mask) {
-    if (c1 | c2) {
-        const ulonglong2 *wm = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)w * a.t;
-        const ulonglong2 *km = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)k * a.t;
-        bool p = false;
-#pragma unroll
-        for (uint32_t h = 0; h < 2; ++h) {
-            const uint32_t i = lane + 32 * h;
-            const bool b1 = (c1 >> i) & 1, b2 = (c2 >> i) & 1;
-            if (b1 | b2) {
-                ++n_mask;
-                const ulonglong2 m = wm[i], r = km[i];
-                if (b1 && (((r.x | r.y) & m.x) | (r.x & m.y))) p = true;  // reduction >= 1
-                if (b2 && (r.x & m.x)) p = true;                          // reduction 2
-            }
-        }
-        if (__any_sync(FULL, p)) return true;
-    }
-    if (len == 0) return false;
-    const unsigned long long tb = a.ht_off[slot], te = a.ht_off[slot + 1];
-    const bool use_ht = te > tb && te <= a.ht_cap;  // else the table was not built
-    const uint32_t mask = (uint32_t)(te - tb) - 1;
-    const uint32_t *ht = a.ht + tb;
-    const uint32_t *rlab = a.pool + rlab_off;
-    const uint32_t *lab = a.pool + lab_off;
-    for (uint32_t j = 0; j < len; j += 32) {
-        bool p = false;
-        if (j + lane < len) {
-            ++n_scan;
-            const uint32_t e = lab[j + lane], h = entry_hub(e);
-            uint32_t tk = INF8;
-            if (use_ht) {
-                uint32_t s = ht_slot(h, mask);
-                for (;;) {
-                    const uint32_t y = ht[s];
-                    if (y == HT_EMPTY) break;
-                    if (entry_hub(y) == h) { tk = entry_dist(y); break; }
-                    s = (s + 1) & mask;
-                }
-            } else {
-                uint32_t lo = 0, hi = rlen;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
-                }
-                if (lo < rlen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
-            }
-            p = tk != INF8 && tk + entry_dist(e) <= level;
-        }
-        if (__any_sync(FULL, p)) return true;
-    }
-    return false;
-}
+// The rest of the prune test for 32 candidates per warp (lane j holds
+// candidate j), in two parts:
+//   masks   one candidate with feasible roots at a time: the lanes take the
+//           roots (two each) and compare mask pairs (Sec. 5.3);
+//   labels  the labels L(w) of the candidates the masks did not prune are
+//           laid end to end and the lanes take 32 consecutive entries per
+//           step (lane x's candidate found by a binary search over a warp scan
+//           of the lengths), so short labels do not leave lanes idle and the
+//           chunks of different candidates are in flight together. Each entry
+//           (h, d) is looked up in the root's filter, and only if its bit is
+//           set in the root's hash table T (or, without a table, by a binary
+//           search of L(v_k)); d + T[h] <= level prunes the candidate. A
+//           candidate found pruned takes no further entries.
+// Per-candidate data sits in shared memory for the lanes that work on it.
+struct TestCand {
+    unsigned long long lab_base;  // pool offset of L(w) minus the candidate's first flattened index
+    unsigned long long tb;        // its root's table in the table pool
+    unsigned long long koff;      // L(v_k) in the label pool (binary-search fallback)
+    uint32_t slot, tmask, klen, pad;  // tmask = table slots - 1, NONE without a table
+};
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_batch_test(BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_test(BatchArgs a) {
     const int lane = threadIdx.x & 31;
+    __shared__ TestCand s_cand[BLOCK / 32][32];
+    TestCand *tc = s_cand[threadIdx.x >> 5];
     const unsigned long long b = a.desc->cand_b, e = a.desc->cand_e;
     const uint32_t level = a.desc->level + 1;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -516,34 +499,111 @@ __global__ void __launch_bounds__(BLOCK) k_batch_test(BatchArgs a) {
     for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
          i0 < span; i0 += stride) {
         const uint32_t cnt = (uint32_t)((e - b - i0) < 32 ? (e - b - i0) : 32);
+        const bool valid = (uint32_t)lane < cnt;
         uint64_t mine = 0;
         ulonglong2 mc = make_ulonglong2(0, 0);
-        uint32_t wlen = 0, klen = 0;
-        uint64_t woff = 0, koff = 0;
-        if ((uint32_t)lane < cnt) {  // per-candidate metadata, loaded in parallel
+        uint32_t wlen = 0, klen = 0, slot = 0, w = 0;
+        unsigned long long woff = 0, koff = 0, tb = 0, te = 0;
+        if (valid) {  // per-candidate metadata, loaded in parallel
             mine = a.cand[b + i0 + lane];
             mc = reinterpret_cast<const ulonglong2 *>(a.candc)[b + i0 + lane];
-            const uint32_t w = (uint32_t)mine, k = a.k0 + (uint32_t)(mine >> 32);
+            w = (uint32_t)mine;
+            slot = (uint32_t)(mine >> 32);
+            const uint32_t k = a.k0 + slot;
             wlen = a.lab_len[w];
             woff = a.lab_off[w];
             klen = a.lab_len[k];
             koff = a.lab_off[k];
+            tb = a.ht_off[slot];
+            te = a.ht_off[slot + 1];
         }
-        bool keep = false;
-        for (uint32_t j = 0; j < cnt; ++j) {
-            const uint64_t c = __shfl_sync(FULL, mine, j);
-            const uint32_t slot = (uint32_t)(c >> 32), w = (uint32_t)c;
-            const bool pruned = prune_warp(a, slot, a.k0 + slot, w, level, __shfl_sync(FULL, mc.x, j),
-                                           __shfl_sync(FULL, mc.y, j), __shfl_sync(FULL, wlen, j),
-                                           __shfl_sync(FULL, woff, j), __shfl_sync(FULL, klen, j),
-                                           __shfl_sync(FULL, koff, j), lane, n_scan, n_mask);
-            if (lane == (int)j) keep = !pruned;
+        // ---- masks
+        uint32_t pruned = 0;
+        for (uint32_t m = __ballot_sync(FULL, (mc.x | mc.y) != 0); m; m &= m - 1) {
+            const uint32_t j = __ffs(m) - 1;
+            const uint64_t c1 = __shfl_sync(FULL, mc.x, j), c2 = __shfl_sync(FULL, mc.y, j);
+            const uint32_t wj = __shfl_sync(FULL, w, j), kj = a.k0 + __shfl_sync(FULL, slot, j);
+            const ulonglong2 *wm = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)wj * a.t;
+            const ulonglong2 *km = reinterpret_cast<const ulonglong2 *>(a.bp_m) + (size_t)kj * a.t;
+            bool p = false;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t i = lane + 32 * h;
+                const bool b1 = (c1 >> i) & 1, b2 = (c2 >> i) & 1;
+                if (b1 | b2) {
+                    ++n_mask;
+                    const ulonglong2 mw = wm[i], r = km[i];
+                    if (b1 && (((r.x | r.y) & mw.x) | (r.x & mw.y))) p = true;  // reduction >= 1
+                    if (b2 && (r.x & mw.x)) p = true;                           // reduction 2
+                }
+            }
+            if (__any_sync(FULL, p)) pruned |= 1u << j;
         }
+        // ---- labels, laid end to end over the unpruned candidates
+        const uint32_t len = (valid && !((pruned >> lane) & 1)) ? wlen : 0;
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t excl = incl - len;
+        __syncwarp();  // the previous group is done with tc
+        if (valid) {
+            TestCand c;
+            c.lab_base = woff - excl;
+            c.tb = tb;
+            c.koff = koff;
+            c.slot = slot;
+            c.tmask = (te > tb && te <= a.ht_cap) ? (uint32_t)(te - tb) - 1 : NONE;
+            c.klen = klen;
+            c.pad = 0;
+            tc[lane] = c;
+        }
+        __syncwarp();
+        for (uint32_t x0 = 0; x0 < total; x0 += 32) {
+            const uint32_t x = x0 + lane;
+            uint32_t j = 0;  // owner: the last candidate whose first entry is <= x
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(FULL, excl, j + step) <= x) j += step;
+            bool p = false;
+            if (x < total && !((pruned >> j) & 1)) {
+                ++n_scan;
+                const TestCand &c = tc[j];
+                const uint32_t ent = a.pool[c.lab_base + x], h = entry_hub(ent);
+                const uint32_t fb = filt_bit(h);
+                if ((a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31)) & 1u) {
+                    uint32_t tk = INF8;
+                    if (c.tmask != NONE) {
+                        const uint32_t *ht = a.ht + c.tb;
+                        uint32_t s = ht_slot(h, c.tmask);
+                        for (;;) {
+                            const uint32_t y = ht[s];
+                            if (y == HT_EMPTY) break;
+                            if (entry_hub(y) == h) { tk = entry_dist(y); break; }
+                            s = (s + 1) & c.tmask;
+                        }
+                    } else {
+                        const uint32_t *rlab = a.pool + c.koff;
+                        uint32_t lo = 0, hi = c.klen;
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
+                        }
+                        if (lo < c.klen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
+                    }
+                    p = tk != INF8 && tk + entry_dist(ent) <= level;
+                }
+            }
+            pruned |= __reduce_or_sync(FULL, p ? 1u << j : 0u);
+        }
+        const bool keep = valid && !((pruned >> lane) & 1);
         if (__any_sync(FULL, keep)) {
             const unsigned long long pos = warp_append(&a.ctr->out_n, keep, lane);
             if (keep) {
-                const uint32_t slot = (uint32_t)(mine >> 32);
-                if (pos < a.out_cap) a.out[pos] = pack_tuple((uint32_t)mine, a.k0 + slot, level);
+                if (pos < a.out_cap) a.out[pos] = pack_tuple(w, a.k0 + slot, level);
                 else atomicOr(&a.ctr->err, ERR_BUF);
             }
         }

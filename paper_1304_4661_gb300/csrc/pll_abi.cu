@@ -141,6 +141,8 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     const size_t itemp_bytes = ((batch_init_temp_bytes(bmax) + 255) & ~(size_t)255) + ((size_t)bmax + 1) * 8 + 256;
     PLL_CHECK(m_itemp.alloc(itemp_bytes));
     PLL_CHECK(m_bits.alloc((size_t)bmax * 16));
+    DevMem m_filt;
+    PLL_CHECK(m_filt.alloc((size_t)bmax * FILT_WORDS * 4));
     uint64_t cand_cap = caps.cand ? caps.cand : std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
     uint64_t out_cap = caps.out ? caps.out : std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
     size_t temp_bytes = 0;
@@ -223,6 +225,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         a.ht_off = m_htoff.as<unsigned long long>();
         a.ht_cap = ht_cap;
         a.rootbits = m_bits.as<uint64_t>();
+        a.filt = m_filt.as<uint32_t>();
         a.cand = m_cand.as<uint64_t>(); a.candc = m_candc.as<uint64_t>(); a.cand_cap = cand_cap;
         a.out = m_out.as<uint64_t>(); a.out_cap = out_cap;
         a.ctr = d_ctr; a.desc = d_desc;
