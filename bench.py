@@ -43,14 +43,11 @@ WORKLOADS = {
     "rmat16": dict(kind="rmat", scale=16, ef=16, t=64, queries=1_000_000, graph_seed=1, pair_seed=3),
 }
 
-# DRAM bytes per launch of the pruned-BFS kernel measured by ncu, valid only
-# for the kernel source with this hash (else traffic is reported as null).
-PROFILED = {
-    # ncu, all 336 + 336 sweep launches of one R-MAT-20 build at the default
-    # root batch; valid for that launch count
-    "k_batch_expand": {"src_sha": "4d85bff4eab1dcd6", "launches": 336, "dram_bytes_per_launch": 798236397},
-    "k_batch_test": {"src_sha": "4d85bff4eab1dcd6", "launches": 336, "dram_bytes_per_launch": 485875839},
-}
+# DRAM bytes per algorithmic byte of a kernel, measured by ncu over every
+# launch of one build of a smaller R-MAT (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass), valid only for the kernel source with this
+# hash (else traffic is reported as null).
+PROFILED = {}
 
 
 def make_graph(w):
@@ -70,6 +67,23 @@ def describe(w, g):
     return {"workload": _workload_name(w), "n": g.n, "arcs": g.nnz, "t": w["t"], "order": "degree (ties by id)",
             "queries": w["queries"], "pair_seed": w["pair_seed"],
             "l2": "L2 flushed (512 MiB write) between timed steps"}
+
+
+def sequential_work(w, g):
+    """Work counts of the oracle's sequential build of this workload's graph
+    (vertices dequeued, labelled, label entries scanned, arcs of labelled
+    vertices), from its stored digest; None if there is none for it."""
+    if w.get("kind") != "rmat":
+        return None
+    path = os.path.join(ROOT, "tests", "golden", f"rmat{w['scale']}_t{w['t']}_digest.json")
+    try:
+        d = json.load(open(path))
+    except OSError:
+        return None
+    gr = d["graph"]
+    if (gr["seed"], gr["n"], gr["nnz"], gr["edge_factor"]) != (w["graph_seed"], g.n, g.nnz, w["ef"]):
+        return None
+    return d.get("sequential_work")
 
 
 def file_sha(path):
@@ -320,13 +334,26 @@ def run_ours(args, w, ws, rank, local):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     q = w["queries"]
-    tp = (t + 15) // 16 * 16
-    # algorithmic bytes of each kernel over one build (per-unit figures x the
-    # units the kernels count), divided over its launches
-    exp_bytes = (st["pre_cleanup"] * (8 + 8 + tp) + st["pruned_expanded"] * (4 + 4)
-                 + st["visited"] * tp + st["candidates"] * 24)
-    test_bytes = (st["candidates"] * (24 + 24) + st["pruned_masks"] * 16
-                  + st["pruned_scanned"] * (4 + 4) + st["pre_cleanup"] * 8)
+    # algorithmic bytes of each kernel over one build: the per-unit figures of
+    # the method's pruned stage times the units of work the method does. The
+    # units are the counts of the oracle's sequential run (Alg. 1 for every
+    # root, in rank order) where the workload has a stored oracle digest:
+    # vertices dequeued, vertices labelled, label entries scanned by prune
+    # tests, arcs of labelled vertices. Otherwise the GPU's own counters stand
+    # in (they include the root batches' surplus work).
+    seq = sequential_work(w, g)
+    if seq:
+        units, unit_src = seq, "oracle sequential counts (tests/golden digest)"
+    else:
+        units = {"visited": st["visited"], "labeled": st["pre_cleanup"],
+                 "scanned": st["pruned_scanned"], "labeled_deg": st["pruned_expanded"]}
+        unit_src = "GPU counters"
+    # expand: a labelled vertex's neighbour ids (4 per arc) and its entry (4 + 1);
+    # a dequeued vertex's offsets (8) and bit-parallel distance row (t bytes)
+    exp_bytes = 4 * units["labeled_deg"] + 5 * units["labeled"] + (8 + t) * units["visited"]
+    # test: the label entries its prune tests scan (4 bytes each); mask bytes
+    # are not counted (the distance filter of Sec. 5.3 leaves most unread)
+    test_bytes = 4 * units["scanned"]
     # per pair: ids (8), ranks (8), 2 x t distance bytes, 4 label offsets (32),
     # the result byte, and both labels (4 bytes per entry; Lsz is by vertex id)
     q_bytes = q * (8 + 8 + 2 * t + 32 + 1) + 4 * int(Lsz[s].sum() + Lsz[u].sum())
@@ -348,13 +375,15 @@ def run_ours(args, w, ws, rank, local):
     src = os.path.join(ROOT, "paper_1304_4661_gb300", "csrc",
                        "k_query.cu" if dom == "k_query" else "k_pruned.cu")
     prof = PROFILED.get(dom)
-    traffic = (prof["dram_bytes_per_launch"]
-               if prof and prof["src_sha"] == file_sha(src) and prof.get("launches") == kd["launches"]
-               else None)
+    # DRAM bytes per algorithmic byte, measured by ncu on a smaller graph of the
+    # same family with this kernel source, scaled to this launch's bytes
+    traffic = (round(prof["dram_per_alg_byte"] * kd["bytes_per_launch"])
+               if prof and prof["src_sha"] == file_sha(src) else None)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": round(kd["bytes_per_launch"]),
+                "units": unit_src,
                 "launch_ms": round(kd["ms_per_launch"], 4),
                 "others": {k: {"achieved_gbs": round(v["achieved_gbs"], 1),
                                "ms_per_step": round(v["ms_per_step"], 3), "launches": v["launches"]}

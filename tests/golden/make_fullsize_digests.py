@@ -37,6 +37,8 @@ CONFIGS = {
     "rmat21": (21, 5, 64, 10_000_000, 3),   # the learned-order evaluation graph, Degree order
     "rmat22": (22, 6, 64, 10_000_000, 3),   # the served index
     "rmat16": (16, 1, 64, 1_000_000, 3),    # a small case of the same recipe (quick self-check)
+    "rmat18": (18, 1, 64, 1_000_000, 3),    # the profiling cases of the sweeps
+    "rmat19": (19, 1, 64, 1_000_000, 3),
 }
 BLOCK = 1 << 16  # vertices per label block digest
 

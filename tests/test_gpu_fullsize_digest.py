@@ -24,7 +24,7 @@ from .gpu_util import dev_u32, gpu_build
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-NAMES = ["rmat16_t64", "rmat20_t64", "rmat21_t64", "rmat22_t64"]
+NAMES = ["rmat16_t64", "rmat18_t64", "rmat19_t64", "rmat20_t64", "rmat21_t64", "rmat22_t64"]
 
 
 def sha(a):
