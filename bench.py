@@ -357,13 +357,25 @@ def run_ours(args, w, ws, rank, local):
     # per pair: ids (8), ranks (8), 2 x t distance bytes, 4 label offsets (32),
     # the result byte, and both labels (4 bytes per entry; Lsz is by vertex id)
     q_bytes = q * (8 + 8 + 2 * t + 32 + 1) + 4 * int(Lsz[s].sum() + Lsz[u].sum())
-    kern = {
-        "k_batch_test": {"ms_per_step": st["ms_test"], "launches": st["test_launches"],
-                         "bytes": test_bytes},
-        "k_batch_expand": {"ms_per_step": st["ms_expand"], "launches": st["expand_launches"],
-                           "bytes": exp_bytes},
-        "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes": q_bytes},
-    }
+    if st["levels_launches"]:
+        # one cooperative launch per root batch runs both sweeps of every level;
+        # its phases' wall times split the time between them
+        kern = {
+            "k_batch_levels": {"ms_per_step": st["ms_levels"], "launches": st["levels_launches"],
+                               "bytes": exp_bytes + test_bytes},
+            "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes": q_bytes},
+        }
+        phases = {"expand": {"ms_per_step": st["ms_expand"], "bytes": exp_bytes},
+                  "test": {"ms_per_step": st["ms_test"], "bytes": test_bytes}}
+    else:
+        kern = {
+            "k_batch_test": {"ms_per_step": st["ms_test"], "launches": st["test_launches"],
+                             "bytes": test_bytes},
+            "k_batch_expand": {"ms_per_step": st["ms_expand"], "launches": st["expand_launches"],
+                               "bytes": exp_bytes},
+            "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes": q_bytes},
+        }
+        phases = {}
     for v in kern.values():
         v["launches"] = max(v["launches"], 1)
         v["bytes_per_launch"] = v["bytes"] / v["launches"]
@@ -387,7 +399,10 @@ def run_ours(args, w, ws, rank, local):
                 "launch_ms": round(kd["ms_per_launch"], 4),
                 "others": {k: {"achieved_gbs": round(v["achieved_gbs"], 1),
                                "ms_per_step": round(v["ms_per_step"], 3), "launches": v["launches"]}
-                           for k, v in kern.items()}}
+                           for k, v in kern.items()},
+                "phases": {k: {"ms_per_step": round(v["ms_per_step"], 3),
+                               "achieved_gbs": round(v["bytes"] / max(v["ms_per_step"], 1e-9) / 1e6, 1)}
+                           for k, v in phases.items()}}
 
     out = {
         "metric": METRIC, "value": round(build_ms / 1e3, 6), "unit": "s", "n_gpus": ws,
@@ -405,6 +420,7 @@ def run_ours(args, w, ws, rank, local):
         "phases_ms": {"prep": round(st["ms_prep"], 3), "bp": round(st["ms_bp"], 3),
                       "pruned": round(st["ms_pruned"], 3), "pruned_bfs": round(st["ms_pruned_kernel"], 3),
                       "expand_sweeps": round(st["ms_expand"], 3), "test_sweeps": round(st["ms_test"], 3),
+                      "level_loop": round(st["ms_levels"], 3),
                       "finalize": round(st["ms_finalize"], 3)},
         "batches": st["batches"], "pre_cleanup": st["pre_cleanup"], "visited": st["visited"],
         "prune_work": {"label_entries_scanned": st["pruned_scanned"], "mask_pairs": st["pruned_masks"],

@@ -66,6 +66,13 @@ typedef enum pll_status {
 typedef struct pll_index pll_index;
 
 /* Build options. Zero-initialise and set what you need. */
+/* pll_build_opts.flags: the host enqueues the levels of each root batch as
+ * separate launches and reads a counter block back every few levels, instead
+ * of one cooperative launch that runs every level of the batch on the device.
+ * Same labels either way; also taken when the device cannot launch
+ * cooperatively. */
+#define PLL_BUILD_HOST_LEVELS 1u
+
 typedef struct pll_build_opts {
     uint32_t t;          /* bit-parallel roots, 0..PLL_MAX_T (Sec. 5.4). */
     uint32_t root_batch; /* largest number of pruned-BFS roots processed in
@@ -75,7 +82,7 @@ typedef struct pll_build_opts {
                             gives the same labels. */
     uint32_t block;      /* threads per CTA of the pruned-BFS kernel: 128,
                             256, 512 or 1024; 0 = library default (256). */
-    uint32_t flags;      /* reserved, must be 0. */
+    uint32_t flags;      /* 0, or PLL_BUILD_HOST_LEVELS. */
     uint64_t reserved;   /* must be 0. */
 } pll_build_opts;
 
@@ -115,6 +122,11 @@ typedef struct pll_stats {
     uint64_t pool_regrows;       /* times the label pool was moved to a larger one */
     uint64_t table_fallbacks;    /* batches whose root tables did not all fit
                                     (those roots' labels were binary-searched) */
+    /* the device-side level loop (one cooperative launch per root batch; 0
+       under PLL_BUILD_HOST_LEVELS): its launches and their CUDA-event time.
+       ms_expand / ms_test are then the wall times of its two phases. */
+    uint64_t levels_launches;
+    double ms_levels;
 } pll_stats;
 
 /*
@@ -597,6 +609,15 @@ PLL_API int64_t pll_test_live_allocs(void);
  * counts appear in pll_stats.
  */
 PLL_API void pll_test_capacities(uint64_t cand, uint64_t out, uint64_t pool, uint64_t tables);
+
+/*
+ * Test hook for the bounded waits of the device-side level loop; the paper has
+ * no counterpart. pll_test_barrier_timeout(ns) sets the longest time a CTA
+ * waits at one grid barrier of later builds (0 = the default of 10 s). A wait
+ * that runs out makes the build return PLL_E_TIMEOUT, with every CTA gone from
+ * the kernel and the context usable. Process-wide.
+ */
+PLL_API void pll_test_barrier_timeout(uint64_t ns);
 
 /* Static, human-readable text for a status code. */
 PLL_API const char *pll_status_str(int status);

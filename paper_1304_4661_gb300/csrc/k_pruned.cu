@@ -386,21 +386,20 @@ __device__ __forceinline__ void append_cand(const BatchArgs &a, bool keep, int l
 // root's row, the same for every lane, sits once per warp in shared memory).
 // 1280 threads per SM (48 registers a thread): the sweep hides the latency of
 // its row and visited-word loads with resident warps.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs a) {
+// The sweep over entries [b, e) of level `level` by the warps of a grid;
+// kr: this warp's row in shared memory. Adds the arcs it scans and the
+// vertices it tests to nexp / nreach.
+__device__ __forceinline__ void expand_body(const BatchArgs &a, unsigned long long b, unsigned long long e,
+                                            uint32_t level, uint4 *kr, uint32_t &nexp, uint32_t &nreach) {
     const int lane = threadIdx.x & 31;
-    extern __shared__ uint4 s_rows[];
-    uint4 *kr = s_rows + (size_t)(threadIdx.x >> 5) * (PLL_MAX_T / 16);
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long b = a.desc->lvl_b, e = a.desc->lvl_e;
-    const uint32_t level = a.desc->level, nq = a.tp >> 4;
+    const uint32_t nq = a.tp >> 4;
     const uint32_t nlevel = level + 1;                // level of the candidates
     const bool fast = nlevel <= FAST_LEVEL;           // clamped rows, plain arithmetic
     const bool near = nlevel + 2 >= INF8;             // byte sums could overflow
     const uint32_t lv = fast ? (0x80u + nlevel) * 0x01010101u : nlevel * 0x01010101u;
     const uint8_t *rows = fast ? a.bp_c : a.bp_d;
-    uint32_t nexp = 0, nreach = 0;
     for (unsigned long long j = b + gw; j < e; j += nwarps) {
         const uint64_t key = a.out[j];
         const uint32_t u = (uint32_t)(key >> 32);
@@ -422,13 +421,26 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs 
             append_cand(a, keep, lane, slot, w, c1, c2);
         }
     }
+}
+
+// warp sums of the work counters into ctr->work[w0], ctr->work[w0 + 1]
+__device__ __forceinline__ void flush_work(const BatchArgs &a, int w0, uint32_t x, uint32_t y) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        nexp += __shfl_xor_sync(FULL, nexp, o);
-        nreach += __shfl_xor_sync(FULL, nreach, o);
+        x += __shfl_xor_sync(FULL, x, o);
+        y += __shfl_xor_sync(FULL, y, o);
     }
-    if (lane == 0 && nexp) atomicAdd(&a.ctr->work[2], (unsigned long long)nexp);
-    if (lane == 0 && nreach) atomicAdd(&a.ctr->work[3], (unsigned long long)nreach);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&a.ctr->work[w0], (unsigned long long)x);
+    if ((threadIdx.x & 31) == 0 && y) atomicAdd(&a.ctr->work[w0 + 1], (unsigned long long)y);
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand(BatchArgs a) {
+    extern __shared__ uint4 s_rows[];
+    uint32_t nexp = 0, nreach = 0;
+    expand_body(a, a.desc->lvl_b, a.desc->lvl_e, a.desc->level,
+                s_rows + (size_t)(threadIdx.x >> 5) * (PLL_MAX_T / 16), nexp, nreach);
+    flush_work(a, 2, nexp, nreach);
 }
 
 template <int BLOCK>
@@ -485,15 +497,13 @@ struct TestCand {
     uint32_t slot, tmask, klen, pad;  // tmask = table slots - 1, NONE without a table
 };
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_test(BatchArgs a) {
+// The sweep over candidates [b, e) of level `level` by the warps of a grid;
+// tc: this warp's 32 records in shared memory. Adds the label entries it scans
+// and the mask pairs it reads to n_scan / n_mask.
+__device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long b, unsigned long long e,
+                                          uint32_t level, TestCand *tc, uint32_t &n_scan, uint32_t &n_mask) {
     const int lane = threadIdx.x & 31;
-    __shared__ TestCand s_cand[BLOCK / 32][32];
-    TestCand *tc = s_cand[threadIdx.x >> 5];
-    const unsigned long long b = a.desc->cand_b, e = a.desc->cand_e;
-    const uint32_t level = a.desc->level + 1;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    uint32_t n_scan = 0, n_mask = 0;
     // warp-uniform trip count: each warp takes 32 consecutive candidates
     const unsigned long long span = ((e - b + 31) / 32) * 32;
     for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
@@ -608,14 +618,105 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_test(BatchArgs a)
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n_scan += __shfl_xor_sync(FULL, n_scan, o);
-        n_mask += __shfl_xor_sync(FULL, n_mask, o);
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_test(BatchArgs a) {
+    __shared__ TestCand s_cand[BLOCK / 32][32];
+    uint32_t n_scan = 0, n_mask = 0;
+    test_body(a, a.desc->cand_b, a.desc->cand_e, a.desc->level + 1, s_cand[threadIdx.x >> 5], n_scan, n_mask);
+    flush_work(a, 0, n_scan, n_mask);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident). The last
+// CTA to arrive takes a snapshot of the counters (error word, candidate and
+// entry counts) before it releases the others, so every CTA decides the next
+// step from the same values. A wait longer than the state's timeout_ns sets
+// ERR_TIMEOUT and returns false: the CTA leaves the level loop, and the
+// others leave it at their next barrier, each wait bounded the same way.
+__device__ __forceinline__ bool grid_barrier(const BatchArgs &a, LoopState *ls) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned int gen = *(volatile unsigned int *)&ls->gen;
+        if (atomicAdd(&ls->count, 1u) == gridDim.x - 1) {
+            ls->count = 0;
+            ls->err = atomicOr(&a.ctr->err, 0u);
+            ls->cand_n = atomicAdd(&a.ctr->cand_n, 0ull);
+            ls->out_n = atomicAdd(&a.ctr->out_n, 0ull);
+            __threadfence();
+            atomicAdd(&ls->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns(), lim = ls->timeout_ns;
+            while (*(volatile unsigned int *)&ls->gen == gen) {
+                if (global_ns() - t0 > lim) {
+                    atomicOr(&a.ctr->err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
     }
-    if (lane == 0 && (n_scan | n_mask)) {
-        atomicAdd(&a.ctr->work[0], (unsigned long long)n_scan);
-        atomicAdd(&a.ctr->work[1], (unsigned long long)n_mask);
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Every level of a root batch in one cooperative launch: expand, barrier,
+// test, barrier, until the frontier is empty (or a buffer overflows, a depth
+// reaches 255, or a barrier times out). Level bounds live in registers, the
+// same in every CTA (they come from the barrier's snapshots), so no level
+// needs the host. Block 0 adds the phases' wall times to the loop state.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_levels(BatchArgs a) {
+    extern __shared__ uint4 s_rows[];
+    __shared__ TestCand s_cand[BLOCK / 32][32];
+    LoopState *ls = a.loop;
+    uint4 *kr = s_rows + (size_t)(threadIdx.x >> 5) * (PLL_MAX_T / 16);
+    TestCand *tc = s_cand[threadIdx.x >> 5];
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long lvl_b = a.desc->lvl_b, lvl_e = a.desc->lvl_e, cand_e = 0;
+    uint32_t level = 0, nexp = 0, nreach = 0, n_scan = 0, n_mask = 0;
+    unsigned long long ns_e = 0, ns_t = 0;
+    constexpr uint32_t STOP = ERR_DEPTH | ERR_BUF | ERR_TIMEOUT;
+    while (lvl_b < lvl_e) {
+        const unsigned long long t0 = timer ? global_ns() : 0;
+        expand_body(a, lvl_b, lvl_e, level, kr, nexp, nreach);
+        if (!grid_barrier(a, ls)) break;
+        const unsigned long long t1 = timer ? global_ns() : 0;
+        if (*(volatile uint32_t *)&ls->err & STOP) break;
+        const unsigned long long cand_b = cand_e;
+        const unsigned long long cn = *(volatile unsigned long long *)&ls->cand_n;
+        cand_e = cn < a.cand_cap ? cn : a.cand_cap;
+        test_body(a, cand_b, cand_e, level + 1, tc, n_scan, n_mask);
+        if (!grid_barrier(a, ls)) break;
+        if (timer) {
+            const unsigned long long t2 = global_ns();
+            ns_e += t1 - t0;
+            ns_t += t2 - t1;
+        }
+        if (*(volatile uint32_t *)&ls->err & STOP) break;
+        const unsigned long long on = *(volatile unsigned long long *)&ls->out_n;
+        lvl_b = lvl_e;
+        lvl_e = on < a.out_cap ? on : a.out_cap;
+        ++level;
+    }
+    flush_work(a, 2, nexp, nreach);
+    flush_work(a, 0, n_scan, n_mask);
+    if (timer) {
+        ls->ns_expand += ns_e;
+        ls->ns_test += ns_t;
+        ls->levels += level;
     }
 }
 
@@ -716,6 +817,53 @@ int batch_clamp_rows(const uint8_t *bp_d, uint8_t *bp_c, size_t bytes, int grid,
 int batch_clear(const BatchArgs &a, int grid, cudaStream_t s) {
     k_batch_clear<<<grid > 0 ? grid : 1, 256, 0, s>>>(a);
     PLL_TRY(cudaGetLastError());
+    return PLL_OK;
+}
+
+template <int BLOCK>
+static cudaError_t levels_grid(int *grid) {
+    int dev = 0, sms = 0, coop = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_levels<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)expand_smem<BLOCK>());
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_levels<BLOCK>, BLOCK, expand_smem<BLOCK>());
+    *grid = (e == cudaSuccess && coop && per > 0) ? sms * per : 0;
+    return e;
+}
+
+int batch_levels_grid(uint32_t block, int *grid) {
+    cudaError_t e;
+    switch (block) {
+        case 128: e = levels_grid<128>(grid); break;
+        case 512: e = levels_grid<512>(grid); break;
+        case 1024: e = levels_grid<1024>(grid); break;
+        default: e = levels_grid<256>(grid); break;
+    }
+    PLL_TRY(e);
+    return PLL_OK;
+}
+
+template <int BLOCK>
+static cudaError_t launch_levels(const BatchArgs &a, int grid, cudaStream_t s) {
+    BatchArgs arg = a;
+    void *args[] = {&arg};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_batch_levels<BLOCK>), dim3(grid),
+                                       dim3(BLOCK), args, expand_smem<BLOCK>(), s);
+}
+
+int batch_levels(const BatchArgs &a, uint32_t block, int grid, cudaStream_t s) {
+    cudaError_t e;
+    switch (block) {
+        case 128: e = launch_levels<128>(a, grid, s); break;
+        case 512: e = launch_levels<512>(a, grid, s); break;
+        case 1024: e = launch_levels<1024>(a, grid, s); break;
+        default: e = launch_levels<256>(a, grid, s); break;
+    }
+    PLL_TRY(e);
     return PLL_OK;
 }
 

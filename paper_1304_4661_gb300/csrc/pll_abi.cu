@@ -37,6 +37,7 @@ int err_to_status(uint32_t err) {
     if (err & ERR_ORDER) return PLL_E_ORDER;
     if (err & ERR_DEPTH) return PLL_E_RANGE;
     if (err & ERR_POOL) return PLL_E_NOMEM;
+    if (err & ERR_TIMEOUT) return PLL_E_TIMEOUT;
     return PLL_OK;
 }
 
@@ -91,7 +92,7 @@ struct Timer {
 
 // Step 3: batched pruned BFS + cleanup + append, then step 4.
 int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, const uint8_t *inX,
-                 uint32_t bmax, uint32_t block, cudaStream_t s) {
+                 uint32_t bmax, uint32_t block, bool host_levels, cudaStream_t s) {
     const uint32_t n = ix->n;
     LabelStore st;
     st.n = n;
@@ -123,6 +124,20 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
 
     int grid[2] = {0, 0};
     PLL_CHECK(batch_grid(block, grid));
+    // the device-side level loop: one cooperative launch per batch (the host
+    // enqueues the levels itself when asked to, or when the device cannot
+    // launch cooperatively)
+    int lgrid = 0;
+    if (!host_levels) PLL_CHECK(batch_levels_grid(block, &lgrid));
+    const bool device_levels = lgrid > 0;
+    DevMem m_loop;
+    PLL_CHECK(m_loop.alloc(sizeof(LoopState)));
+    LoopState *d_loop = m_loop.as<LoopState>();
+    {
+        LoopState init{};
+        init.timeout_ns = test_barrier_timeout_ns();
+        PLL_TRY(cudaMemcpyAsync(d_loop, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    }
     // clamped copy of the bit-parallel distance rows for the expand sweep
     DevMem m_bpc;
     PLL_CHECK(m_bpc.alloc(std::max<size_t>((size_t)n * ix->tp, 16)));
@@ -228,17 +243,26 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         a.filt = m_filt.as<uint32_t>();
         a.cand = m_cand.as<uint64_t>(); a.candc = m_candc.as<uint64_t>(); a.cand_cap = cand_cap;
         a.out = m_out.as<uint64_t>(); a.out_cap = out_cap;
-        a.ctr = d_ctr; a.desc = d_desc;
+        a.ctr = d_ctr; a.desc = d_desc; a.loop = d_loop;
         PLL_TRY(cudaEventRecord(ev0, s));
         PLL_TRY(cudaMemsetAsync(d_ctr, 0, 16, s));  // cand_n, out_n
         PLL_TRY(cudaMemsetAsync(&d_ctr->err, 0, 4, s));
         PLL_CHECK(batch_init(a, m_itemp.p, itemp_bytes, s));
         ix->stats.launches += 3;
         ix->stats.cub_calls += 1;
-        // enqueue levels ahead; read back only to find the empty frontier.
+        if (device_levels) {
+            // every level of the batch in one launch; events around it
+            PLL_TRY(cudaMemsetAsync(&d_loop->count, 0, 4, s));
+            PLL_TRY(cudaEventRecord(sweep_ev[0], s));
+            PLL_CHECK(batch_levels(a, block, lgrid, s));
+            PLL_TRY(cudaEventRecord(sweep_ev[1], s));
+            ix->stats.launches += 1;
+            ix->stats.levels_launches += 1;
+        }
+        // or: enqueue levels ahead; read back only to find the empty frontier.
         // Events around every expand and test sweep give their device times.
         uint32_t ahead = 4;
-        for (;;) {
+        for (; !device_levels;) {
             for (uint32_t l = 0; l < ahead; ++l)
                 PLL_CHECK(batch_level(a, grid, block, s, sweep_ev + 4 * l));
             ix->stats.launches += 4ull * ahead;
@@ -270,7 +294,12 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             PLL_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
             ix->stats.ms_pruned_kernel += ms;
             ix->stats.pruned_launches += 1;
+            if (device_levels) {
+                PLL_TRY(cudaEventElapsedTime(&ms, sweep_ev[0], sweep_ev[1]));
+                ix->stats.ms_levels += ms;
+            }
         }
+        if (h->c.err & ERR_TIMEOUT) return PLL_E_TIMEOUT;
         if (h->c.err & ERR_DEPTH) return PLL_E_RANGE;
         if (h->c.err & ERR_TABLE) {  // some root tables did not fit: those roots were
             // binary-searched (same answers); grow the pool for later batches
@@ -336,6 +365,15 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         k0 = k1;
         B = std::min<uint32_t>(B * 2, bmax);
     }
+    if (device_levels) {  // phase times and level counts of the device-side loop
+        LoopState ls{};
+        PLL_TRY(cudaMemcpyAsync(&ls, d_loop, sizeof(ls), cudaMemcpyDeviceToHost, s));
+        PLL_TRY(cudaStreamSynchronize(s));
+        ix->stats.ms_expand = ls.ns_expand * 1e-6;
+        ix->stats.ms_test = ls.ns_test * 1e-6;
+        ix->stats.expand_launches = ls.levels;
+        ix->stats.test_launches = ls.levels;
+    }
     ix->stats.pruned_scanned = h->c.work[0];
     ix->stats.pruned_masks = h->c.work[1];
     ix->stats.pruned_expanded = h->c.work[2];
@@ -370,7 +408,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (opts) o = *opts;
     if (!out) return PLL_E_INVAL;
     *out = nullptr;
-    if (o.reserved != 0 || o.flags != 0) return PLL_E_INVAL;
+    if (o.reserved != 0 || (o.flags & ~PLL_BUILD_HOST_LEVELS) != 0) return PLL_E_INVAL;
     if (o.t > PLL_MAX_T) return PLL_E_RANGE;
     if (n > MAX_N || nnz >= 0xffffffffull) return PLL_E_RANGE;
     if (n > 0 && !off) return PLL_E_INVAL;
@@ -494,7 +532,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     // ---- 3 + 4. pruned labels
     tm.start();
     PLL_CHECK(pruned_stage(ix, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), m_inX.as<uint8_t>(),
-                           bmax, block, s));
+                           bmax, block, (o.flags & PLL_BUILD_HOST_LEVELS) != 0, s));
     ix->stats.ms_pruned = tm.stop_ms();
 
     PLL_TRY(dev_malloc(&ix->d_qerr, 16));
@@ -558,6 +596,15 @@ bool alloc_should_fail() {
 }
 
 void alloc_note(long long delta) { g_live.fetch_add(delta, std::memory_order_relaxed); }
+
+// longest wait of a grid barrier of the level loop (test hook; 0 = default)
+static std::atomic<uint64_t> g_barrier_ns{0};
+constexpr uint64_t BARRIER_TIMEOUT_NS = 10ull * 1000 * 1000 * 1000;  // 10 s
+
+uint64_t test_barrier_timeout_ns() {
+    const uint64_t v = g_barrier_ns.load(std::memory_order_relaxed);
+    return v ? v : BARRIER_TIMEOUT_NS;
+}
 
 // test capacities of the pruned stage (0 = the library's own sizing)
 static std::atomic<uint64_t> g_cap_cand{0}, g_cap_out{0}, g_cap_pool{0}, g_cap_ht{0};
@@ -820,6 +867,8 @@ PLL_API void pll_free(pll_index *idx) { free_index(idx); }
 PLL_API void pll_test_fail_alloc(int64_t k) { g_fail_after.store(k < 0 ? -1 : k); }
 
 PLL_API int64_t pll_test_live_allocs(void) { return g_live.load(); }
+
+PLL_API void pll_test_barrier_timeout(uint64_t ns) { g_barrier_ns.store(ns); }
 
 PLL_API void pll_test_capacities(uint64_t cand, uint64_t out, uint64_t pool, uint64_t tables) {
     g_cap_cand.store(cand);

@@ -102,6 +102,8 @@ struct TestCaps {
     uint64_t cand = 0, out = 0, pool = 0, ht = 0;
 };
 TestCaps test_caps();
+// longest wait of a grid barrier of the level loop, ns (pll_test_barrier_timeout)
+uint64_t test_barrier_timeout_ns();
 template <class T> inline cudaError_t dev_malloc(T **p, size_t b) {
     *p = nullptr;
     if (alloc_should_fail()) return cudaErrorMemoryAllocation;
@@ -216,7 +218,19 @@ struct BatchCounters {
     uint32_t err;
     uint32_t pad;
 };
-constexpr uint32_t ERR_TABLE = 1u << 5;  // root hash-table pool too small
+constexpr uint32_t ERR_TABLE = 1u << 5;    // root hash-table pool too small
+constexpr uint32_t ERR_TIMEOUT = 1u << 6;  // a grid barrier waited past its limit
+
+// State of the device-side level loop (k_batch_levels): a grid barrier and
+// the snapshots its last CTA takes; phase times summed over the build.
+struct LoopState {
+    unsigned int count, gen;            // barrier arrivals, generation
+    unsigned int err, pad;              // snapshot of BatchCounters::err
+    unsigned long long cand_n, out_n;   // snapshots of the counts
+    unsigned long long timeout_ns;      // longest barrier wait
+    unsigned long long ns_expand, ns_test;  // phase wall times (block 0)
+    unsigned long long levels;          // levels run
+};
 
 struct LevelDesc {
     unsigned long long lvl_b, lvl_e;    // entries of the current level
@@ -251,12 +265,17 @@ struct BatchArgs {
     unsigned long long out_cap;
     BatchCounters *ctr;
     LevelDesc *desc;
+    LoopState *loop;           // device-side level loop (k_batch_levels)
 };
 int batch_grid(uint32_t block, int *grid);  // grid[2]: expand, test
 int batch_init(const BatchArgs &a, void *temp, size_t temp_bytes, cudaStream_t s);
 size_t batch_init_temp_bytes(uint32_t bmax);
 int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_t s,
                 cudaEvent_t *ev);
+// all levels of a batch in one cooperative launch (grid from
+// batch_levels_grid; 0 there means cooperative launches are unavailable)
+int batch_levels_grid(uint32_t block, int *grid);
+int batch_levels(const BatchArgs &a, uint32_t block, int grid, cudaStream_t s);
 // lazy reset of the visited bitmap after a batch: clears the words of the
 // roots and of every recorded candidate (all bits the batch set)
 int batch_clear(const BatchArgs &a, int grid, cudaStream_t s);

@@ -32,6 +32,7 @@ SYMBOLS = [
     "pll_mlp_set_params", "pll_mlp_get_params", "pll_mlp_forward", "pll_mlp_grad",
     "pll_mlp_read_grad", "pll_mlp_adam", "pll_mlp_train_step", "pll_learned_order",
     "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs", "pll_test_capacities",
+    "pll_test_barrier_timeout",
     "pll_paths_create", "pll_paths_parents", "pll_path_offsets", "pll_path_query",
     "pll_paths_free",
     "pll_build_directed", "pll_dquery", "pll_dlabel_entries", "pll_dexport_labels",
@@ -39,6 +40,9 @@ SYMBOLS = [
 ]
 MLP_NPARAM = 4801
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+PLL_BUILD_HOST_LEVELS = 1  # pll_build_opts.flags: levels enqueued by the host
 
 
 class BuildOpts(C.Structure):
@@ -59,7 +63,8 @@ class Stats(C.Structure):
                 ("expand_launches", C.c_uint64), ("test_launches", C.c_uint64),
                 ("candidates", C.c_uint64), ("graphs", C.c_uint32), ("reserved32", C.c_uint32),
                 ("redone_batches", C.c_uint64), ("pool_regrows", C.c_uint64),
-                ("table_fallbacks", C.c_uint64)]
+                ("table_fallbacks", C.c_uint64), ("levels_launches", C.c_uint64),
+                ("ms_levels", C.c_double)]
 
 
 class ServerOpts(C.Structure):
@@ -196,6 +201,8 @@ def load(build_if_missing: bool = True):
     lib.pll_test_live_allocs.argtypes = []
     lib.pll_test_capacities.restype = None
     lib.pll_test_capacities.argtypes = [C.c_uint64] * 4
+    lib.pll_test_barrier_timeout.restype = None
+    lib.pll_test_barrier_timeout.argtypes = [C.c_uint64]
     _lib = lib
     return lib
 
@@ -306,10 +313,10 @@ class Index:
     # ------------------------------------------------------------- build
     @classmethod
     def build(cls, offsets, cols, t: int = 0, order=None, root_batch: int = 0, block: int = 0,
-              stream=None) -> "Index":
+              stream=None, flags: int = 0) -> "Index":
         """pll_build (CUDA tensors) or pll_build_host (numpy arrays)."""
         lib = load()
-        opts = BuildOpts(t, root_batch, block, 0, 0)
+        opts = BuildOpts(t, root_batch, block, flags, 0)
         out = C.c_void_p()
         n = int(offsets.shape[0]) - 1
         nnz = int(cols.shape[0])
@@ -333,11 +340,11 @@ class Index:
 
     @classmethod
     def build_batch(cls, offsets, cols, graph_start, t: int = 0, root_batch: int = 0,
-                    block: int = 0, stream=None) -> "Index":
+                    block: int = 0, stream=None, flags: int = 0) -> "Index":
         """pll_build_batch: CUDA tensors for the union CSR, graph_start as a
         host uint32 array of graphs + 1 vertex boundaries."""
         lib = load()
-        opts = BuildOpts(t, root_batch, block, 0, 0)
+        opts = BuildOpts(t, root_batch, block, flags, 0)
         out = C.c_void_p()
         n = int(offsets.shape[0]) - 1
         nnz = int(cols.shape[0])

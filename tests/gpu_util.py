@@ -13,11 +13,11 @@ def dev_u32(a):
     return torch.from_numpy(a.view(np.int32)).cuda()
 
 
-def gpu_build(g, t, order=None, root_batch=0, block=0):
+def gpu_build(g, t, order=None, root_batch=0, block=0, flags=0):
     from paper_1304_4661_gb300 import pll
     return pll.Index.build(dev_u32(g.offsets), dev_u32(g.cols), t=t,
                            order=None if order is None else dev_u32(order),
-                           root_batch=root_batch, block=block)
+                           root_batch=root_batch, block=block, flags=flags)
 
 
 def gpu_query(ix, s, t):

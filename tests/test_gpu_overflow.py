@@ -110,3 +110,56 @@ def test_finite_distance_beyond_255_is_a_range_error(t):
         ix.query(dev_u32(np.array([0], np.uint32)), dev_u32(np.array([399], np.uint32)))
     assert e.value.code == pll.PLL_E_RANGE
     assert gpu_query(ix, np.array([0, 3], np.uint32), np.array([254, 257], np.uint32)).tolist() == [254, 254]
+
+
+# ---- the device-side level loop (one cooperative launch per root batch)
+
+@pytest.mark.parametrize("make,t,root_batch", [
+    (lambda: gg.ba(3000, 3, 17), 16, 0),
+    (lambda: gg.ba(3000, 3, 17), 16, 7),
+    (lambda: gg.ws(4000, 6, 0.1, 5), 0, 0),
+    (lambda: gg.rmat(13, 16, seed=3), 64, 100),
+    (lambda: graphs.path(255), 2, 0),
+])
+def test_host_and_device_level_loops_give_the_oracle_labels(make, t, root_batch):
+    """Both ways of running a batch's levels (PLL_BUILD_HOST_LEVELS: separate
+    launches enqueued by the host; default: one cooperative launch per batch)
+    give the oracle's labels; the default one really ran."""
+    g = make()
+    ref = oracle.Index(g.offsets, g.cols, t)
+    Lref = ref.labels()
+    for flags in (0, pll.PLL_BUILD_HOST_LEVELS):
+        ix = gpu_build(g, t, root_batch=root_batch, flags=flags)
+        La = ix.labels()
+        assert same_labels(La, Lref), (flags, first_label_diff(La, Lref, g.n))
+        st = ix.stats()
+        if flags:
+            assert st["levels_launches"] == 0
+        elif g.nnz:
+            assert st["levels_launches"] == st["batches"] > 0
+
+
+def test_barrier_wait_that_runs_out_returns_timeout_and_the_gpu_stays_usable():
+    """A grid barrier of the level loop that waits past its limit makes the
+    build return PLL_E_TIMEOUT: the limit is set to 1 ns, so every CTA but the
+    last to arrive gives up at the first barrier and leaves the kernel. No
+    allocation leaks, and the next build (default limit) is exact."""
+    import gc
+    lib = pll.load()
+    g = gg.ba(3000, 3, 2)
+    gc.collect()
+    gc.disable()  # indices of earlier tests must not be freed mid-count
+    try:
+        live = lib.pll_test_live_allocs()
+        lib.pll_test_barrier_timeout(1)
+        try:
+            with pytest.raises(pll.PLLError) as e:
+                gpu_build(g, 16)
+            assert e.value.code == pll.PLL_E_TIMEOUT
+        finally:
+            lib.pll_test_barrier_timeout(0)
+        assert lib.pll_test_live_allocs() == live
+    finally:
+        gc.enable()
+    ix = gpu_build(g, 16)
+    assert same_labels(ix.labels(), oracle.Index(g.offsets, g.cols, 16).labels())
