@@ -401,7 +401,10 @@ __device__ __forceinline__ void expand_body(const BatchArgs &a, unsigned long lo
     const uint32_t lv = fast ? (0x80u + nlevel) * 0x01010101u : nlevel * 0x01010101u;
     const uint8_t *rows = fast ? a.bp_c : a.bp_d;
     for (unsigned long long j = b + gw; j < e; j += nwarps) {
-        const uint64_t key = a.out[j];
+        // entries and candidates are written by other SMs between the phases of
+        // one launch (k_batch_levels): read them from L2, never from a line the
+        // L1 kept from an earlier level
+        const uint64_t key = __ldcg(a.out + j);
         const uint32_t u = (uint32_t)(key >> 32);
         const uint32_t k = entry_hub((uint32_t)key);
         const uint32_t slot = k - a.k0;
@@ -515,8 +518,8 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
         uint32_t wlen = 0, klen = 0, slot = 0, w = 0;
         unsigned long long woff = 0, koff = 0, tb = 0, te = 0;
         if (valid) {  // per-candidate metadata, loaded in parallel
-            mine = a.cand[b + i0 + lane];
-            mc = reinterpret_cast<const ulonglong2 *>(a.candc)[b + i0 + lane];
+            mine = __ldcg(a.cand + b + i0 + lane);
+            mc = __ldcg(reinterpret_cast<const ulonglong2 *>(a.candc) + b + i0 + lane);
             w = (uint32_t)mine;
             slot = (uint32_t)(mine >> 32);
             const uint32_t k = a.k0 + slot;
