@@ -466,11 +466,20 @@ __global__ void k_clamp_rows(const uint4 *bp_d, uint4 *bp_c, size_t n16) {
 }
 
 // Lazy reset: zero the visited words of the batch's roots and candidates (the
-// only bits the batch set; several candidates may share a word)
+// only bits the batch set; several candidates may share a word). A batch whose
+// candidates overflowed their buffer did not record them all: its rows are
+// zeroed whole (it runs again with a larger buffer).
 __global__ void k_batch_clear(BatchArgs a) {
-    const unsigned long long cn = a.ctr->cand_n < a.cand_cap ? a.ctr->cand_n : a.cand_cap;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.ctr->err & ERR_BUF) {
+        const unsigned long long words = (unsigned long long)a.B * a.NW;
+        uint4 *v4 = reinterpret_cast<uint4 *>(a.visited);  // the bitmap is 256-byte aligned
+        for (unsigned long long i = i0; i < words / 4; i += stride) v4[i] = make_uint4(0, 0, 0, 0);
+        for (unsigned long long i = (words & ~3ull) + i0; i < words; i += stride) a.visited[i] = 0;
+        return;
+    }
+    const unsigned long long cn = a.ctr->cand_n < a.cand_cap ? a.ctr->cand_n : a.cand_cap;
     for (unsigned long long i = i0; i < a.B; i += stride)
         a.visited[i * a.NW + ((a.k0 + (uint32_t)i) >> 5)] = 0;
     for (unsigned long long i = i0; i < cn; i += stride) {

@@ -279,14 +279,11 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             if ((h->c.err & (ERR_DEPTH | ERR_BUF)) || h->d.lvl_b == h->d.lvl_e) break;
             ahead = 2;
         }
-        // lazy reset of the visited rows; an overflowed batch did not record all
-        // of its candidates, so its rows are cleared whole before the redo
-        if (h->c.err & ERR_BUF) {
-            PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)a.B * NW * 4, s));
-        } else {
-            PLL_CHECK(batch_clear(a, grid[0], s));
-            ix->stats.launches += 1;
-        }
+        // lazy reset of the visited rows (the kernel reads the error word: an
+        // overflowed batch, which did not record all of its candidates, has
+        // its rows cleared whole before the redo)
+        PLL_CHECK(batch_clear(a, grid[0], s));
+        ix->stats.launches += 1;
         PLL_TRY(cudaEventRecord(ev1, s));
         PLL_CHECK(read_back());
         {
