@@ -47,7 +47,11 @@ WORKLOADS = {
 # launch of one build of a smaller R-MAT (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass), valid only for the kernel source with this
 # hash (else traffic is reported as null).
-PROFILED = {}
+PROFILED = {
+    # R-MAT-18, t = 64: 24 launches, 4.633 GB of DRAM traffic against 6.953 GB of
+    # algorithmic bytes (the oracle's sequential counts)
+    "k_batch_levels": {"src_sha": "82de8c9ee6e66b74", "dram_per_alg_byte": 0.666},
+}
 
 
 def make_graph(w):
