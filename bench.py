@@ -223,7 +223,8 @@ def run_ours(args, w, ws, rank, local):
     def step(record):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        ix = pll.Index.build(off_d, col_d, t=t, root_batch=args.root_batch, block=args.block)
+        ix = pll.Index.build(off_d, col_d, t=t, root_batch=args.root_batch, block=args.block,
+                             flags=args.flags)
         e1.record(stream)
         ix.query(s_d, u_d, out_d)
         e2.record(stream)
@@ -307,7 +308,7 @@ def run_ours(args, w, ws, rank, local):
         for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             tb = time.perf_counter()
-            opts = pll.BuildOpts(t, args.root_batch, args.block, 0, 0)
+            opts = pll.BuildOpts(t, args.root_batch, args.block, args.flags, 0)
             h = C.c_void_p()
             rc = lib.pll_build_host(off_n.ctypes.data, col_n.ctypes.data, g.n, g.nnz, None,
                                     C.byref(opts), None, C.byref(h))
@@ -478,13 +479,13 @@ def run_batch(args, ws, rank, local):
     def sequential():
         total = 0
         for o, c in per:
-            ix = pll.Index.build(o, c, t=t)
+            ix = pll.Index.build(o, c, t=t, flags=args.flags)
             total += ix.label_entries()
             ix.close()
         return total
 
     def batched(rb=0, bl=0):
-        ix = pll.Index.build_batch(d_off, d_col, start, t=t, root_batch=rb, block=bl)
+        ix = pll.Index.build_batch(d_off, d_col, start, t=t, root_batch=rb, block=bl, flags=args.flags)
         e = ix.label_entries()
         ix.close()
         return e
@@ -1135,8 +1136,11 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--directed-scale", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-levels", action="store_true",
+                    help="run each root batch's levels as separate launches (PLL_BUILD_HOST_LEVELS)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    args.flags = 1 if args.host_levels else 0  # PLL_BUILD_HOST_LEVELS
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload in ("batch256", "serve", "learned", "variants", "paths", "directed"):

@@ -124,10 +124,11 @@ __device__ __forceinline__ uint32_t label_min(const QueryArgs &a, uint32_t s, ui
 // advanced past the hubs not above it, which can meet nothing that is left.
 // Labels read once, in coalesced 128-byte rows. When one label is more than
 // PLL_MERGE_RATIO times longer, binary searches of its entries (label_min)
-// touch less of it and are used instead.
-__device__ __forceinline__ uint32_t label_min_merge(const QueryArgs &a, uint32_t s, uint32_t t, int lane) {
-    const uint64_t os = a.lab_off[s], ot = a.lab_off[t];
-    const uint32_t ls = (uint32_t)(a.lab_off[s + 1] - os), lt = (uint32_t)(a.lab_off[t + 1] - ot);
+// touch less of it and are used instead. os / ls, ot / lt: the offsets and
+// lengths of L(s) and L(t), already loaded by the caller.
+__device__ __forceinline__ uint32_t label_min_merge_at(const QueryArgs &a, uint32_t s, uint32_t t,
+                                                      uint64_t os, uint32_t ls, uint64_t ot, uint32_t lt,
+                                                      int lane) {
     const uint32_t la = ls <= lt ? ls : lt, lb = ls <= lt ? lt : ls;
     if (la == 0) return BIG;
     if (lb > PLL_MERGE_RATIO * la) return label_min(a, s, t, lane, 0, 32);
@@ -189,24 +190,43 @@ __device__ __forceinline__ void store_answer(const QueryArgs &a, uint64_t qi, ui
     }
 }
 
-// One warp per pair, grid-stride over the pairs.
+// One warp per pair, 32 pairs at a time: lane j first fetches pair j's ids,
+// ranks and label offsets (three dependent loads, now in flight for 32 pairs
+// at once instead of one after another), and answers the trivial pairs; the
+// warp then answers the others one by one from the lanes' registers.
 __global__ void __launch_bounds__(256) k_query(QueryArgs a) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t qi = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; qi < a.q; qi += warps) {
+    for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; q0 < a.q;
+         q0 += warps * 32) {
+        const uint64_t qi = q0 + lane;
         uint32_t s = 0, t = 0, ans = 0;
-        bool bad;
-        if (trivial_pair(a, a.src[qi * a.stride], a.dst[qi * a.stride], &s, &t, &ans, &bad)) {
-            if (lane == 0) {
+        bool bad = false, open = false;
+        uint64_t os = 0, ot = 0;
+        uint32_t ls = 0, lt = 0;
+        if (qi < a.q) {
+            open = !trivial_pair(a, a.src[qi * a.stride], a.dst[qi * a.stride], &s, &t, &ans, &bad);
+            if (open) {
+                os = a.lab_off[s];
+                ot = a.lab_off[t];
+                ls = (uint32_t)(a.lab_off[s + 1] - os);
+                lt = (uint32_t)(a.lab_off[t + 1] - ot);
+            } else {
                 a.out[qi] = (uint8_t)ans;
                 if (bad) atomicAdd(a.err + 1, 1ull);
             }
-            continue;
         }
-        uint32_t td0, td1, dstar;
-        bp_tilde(a, s, t, lane, &td0, &td1, &dstar);
-        const uint32_t best = finish_pair(a, s, t, lane, td0, td1, dstar, label_min_merge(a, s, t, lane));
-        if (lane == 0) store_answer(a, qi, best);
+        for (uint32_t m = __ballot_sync(FULL, open); m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            const uint32_t sj = __shfl_sync(FULL, s, j), tj = __shfl_sync(FULL, t, j);
+            const uint64_t osj = __shfl_sync(FULL, os, j), otj = __shfl_sync(FULL, ot, j);
+            const uint32_t lsj = __shfl_sync(FULL, ls, j), ltj = __shfl_sync(FULL, lt, j);
+            uint32_t td0, td1, dstar;
+            bp_tilde(a, sj, tj, lane, &td0, &td1, &dstar);
+            const uint32_t best = finish_pair(a, sj, tj, lane, td0, td1, dstar,
+                                              label_min_merge_at(a, sj, tj, osj, lsj, otj, ltj, lane));
+            if (lane == 0) store_answer(a, q0 + j, best);
+        }
     }
 }
 
@@ -280,7 +300,7 @@ int query_launch_strided(const pll_index *ix, const uint32_t *d_src, const uint3
     } else if (q <= 4 * R) {
         k_query_wide<2><<<(unsigned)((q + 3) / 4), 256, 0, s>>>(a);
     } else {
-        const uint64_t want = (q * 32 + 255) / 256;
+        const uint64_t want = (q + 255) / 256;  // a block takes 8 groups of 32 pairs per step
         k_query<<<(unsigned)(want < R ? want : R), 256, 0, s>>>(a);
     }
     PLL_TRY(cudaGetLastError());
