@@ -133,12 +133,14 @@ __global__ void k_batch_init(BatchArgs a) {
             a.rootbits[2 * slot + 1] = h01;
         }
         // a 1024-bit filter of L(v_k)'s hubs: most hubs of a candidate's label
-        // are not in the root's, and the filter tells so with one load
+        // are not in the root's, and the filter tells so with one load (for
+        // labels of up to FILT_MAX_LEN entries, where at most 12 % of its bits
+        // are set; longer labels go to the table directly)
         const uint32_t len = a.lab_len[k];
         uint32_t *filt = a.filt + (size_t)slot * FILT_WORDS;
-        filt[lane] = 0;
-        __syncwarp();
-        {
+        if (len <= FILT_MAX_LEN) {
+            filt[lane] = 0;
+            __syncwarp();
             const uint32_t *lab = a.pool + a.lab_off[k];
             for (uint32_t j = lane; j < len; j += 32) {
                 const uint32_t fb = filt_bit(entry_hub(lab[j]));
@@ -497,10 +499,11 @@ __global__ void k_batch_clear(BatchArgs a) {
 //           step (lane x's candidate found by a binary search over a warp scan
 //           of the lengths), so short labels do not leave lanes idle and the
 //           chunks of different candidates are in flight together. Each entry
-//           (h, d) is looked up in the root's filter, and only if its bit is
-//           set in the root's hash table T (or, without a table, by a binary
-//           search of L(v_k)); d + T[h] <= level prunes the candidate. A
-//           candidate found pruned takes no further entries.
+//           (h, d) is looked up in the root's filter (roots with labels of at
+//           most FILT_MAX_LEN entries), and only if its bit is set in the
+//           root's hash table T (or, without a table, by a binary search of
+//           L(v_k)); d + T[h] <= level prunes the candidate. A candidate found
+//           pruned takes no further entries.
 // Per-candidate data sits in shared memory for the lanes that work on it.
 struct TestCand {
     unsigned long long lab_base;  // pool offset of L(w) minus the candidate's first flattened index
@@ -585,6 +588,11 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
         }
         __syncwarp();
         for (uint32_t x0 = 0; x0 < total; x0 += 32) {
+            // skip the rest of the labels of candidates already pruned: start
+            // at the first entry of an unpruned candidate that is still ahead
+            const uint32_t live = __ballot_sync(FULL, len > 0 && !((pruned >> lane) & 1) && excl + len > x0);
+            if (!live) break;
+            x0 = max(x0, __shfl_sync(FULL, excl, __ffs(live) - 1));
             const uint32_t x = x0 + lane;
             uint32_t j = 0;  // owner: the last candidate whose first entry is <= x
 #pragma unroll
@@ -596,7 +604,8 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
                 const TestCand &c = tc[j];
                 const uint32_t ent = a.pool[c.lab_base + x], h = entry_hub(ent);
                 const uint32_t fb = filt_bit(h);
-                if ((a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31)) & 1u) {
+                if (c.klen > FILT_MAX_LEN ||
+                    ((a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31)) & 1u)) {
                     uint32_t tk = INF8;
                     if (c.tmask != NONE) {
                         const uint32_t *ht = a.ht + c.tb;

@@ -193,8 +193,10 @@ __device__ __forceinline__ void store_answer(const QueryArgs &a, uint64_t qi, ui
 // One warp per pair, 32 pairs at a time: lane j first fetches pair j's ids,
 // ranks and label offsets (three dependent loads, now in flight for 32 pairs
 // at once instead of one after another), and answers the trivial pairs; the
-// warp then answers the others one by one from the lanes' registers.
-__global__ void __launch_bounds__(256) k_query(QueryArgs a) {
+// warp then answers the others one by one from the lanes' registers. Eight
+// CTAs per SM (32 registers a thread): the kernel is bound by the latency of
+// its loads, so it wants every resident warp it can get.
+__global__ void __launch_bounds__(256, 8) k_query(QueryArgs a) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; q0 < a.q;

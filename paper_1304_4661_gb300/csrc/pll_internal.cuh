@@ -198,7 +198,8 @@ int bp_run_in(uint32_t n, uint32_t t, const uint32_t *d_roff, const uint32_t *d_
 // k_pruned.cu -- batch-synchronous pruned BFS over roots [k0, k0 + B)
 // root label hash tables: 2 x |L(v_k)| slots rounded up to a power of two,
 // at least HT_MIN; labels longer than HT_MAX / 2 are binary-searched instead
-constexpr uint32_t FILT_WORDS = 32;  // 1024-bit hub filter per root of a batch
+constexpr uint32_t FILT_WORDS = 32;     // 1024-bit hub filter per root of a batch
+constexpr uint32_t FILT_MAX_LEN = 128;  // roots with longer labels have no filter
 constexpr uint32_t HT_MIN = 32;
 constexpr uint32_t HT_MAX = 1u << 16;
 __host__ __device__ inline uint32_t ht_size(uint32_t len) {
