@@ -67,6 +67,10 @@
 namespace pll {
 namespace {
 
+#ifndef LABEL_ROUNDS
+#define LABEL_ROUNDS 4
+#endif
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t HT_EMPTY = 0xffffffffu;
 
@@ -505,6 +509,8 @@ __global__ void k_batch_clear(BatchArgs a) {
 //           L(v_k)); d + T[h] <= level prunes the candidate. A candidate found
 //           pruned takes no further entries.
 // Per-candidate data sits in shared memory for the lanes that work on it.
+constexpr int LU = LABEL_ROUNDS;  // label rounds per step of the test sweep
+
 struct TestCand {
     unsigned long long lab_base;  // pool offset of L(w) minus the candidate's first flattened index
     unsigned long long tb;        // its root's table in the table pool
@@ -587,48 +593,74 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
             tc[lane] = c;
         }
         __syncwarp();
-        for (uint32_t x0 = 0; x0 < total; x0 += 32) {
-            // skip the rest of the labels of candidates already pruned: start
-            // at the first entry of an unpruned candidate that is still ahead
-            const uint32_t live = __ballot_sync(FULL, len > 0 && !((pruned >> lane) & 1) && excl + len > x0);
-            if (!live) break;
-            x0 = max(x0, __shfl_sync(FULL, excl, __ffs(live) - 1));
-            const uint32_t x = x0 + lane;
-            uint32_t j = 0;  // owner: the last candidate whose first entry is <= x
+        // LU rounds of 32 entries per step, in three stages so that the loads of
+        // all rounds are in flight together: the label entries, then the filter
+        // words, then the first table slot of each hub (collision chains and the
+        // binary-search fallback follow one by one)
+        for (uint32_t x0 = 0; x0 < total; x0 += 32 * LU) {
+            uint32_t ent[LU], own[LU], fw[LU];
+            bool act[LU];
 #pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(FULL, excl, j + step) <= x) j += step;
-            bool p = false;
-            if (x < total && !((pruned >> j) & 1)) {
-                ++n_scan;
-                const TestCand &c = tc[j];
-                const uint32_t ent = a.pool[c.lab_base + x], h = entry_hub(ent);
-                const uint32_t fb = filt_bit(h);
-                if (c.klen > FILT_MAX_LEN ||
-                    ((a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31)) & 1u)) {
-                    uint32_t tk = INF8;
-                    if (c.tmask != NONE) {
-                        const uint32_t *ht = a.ht + c.tb;
-                        uint32_t s = ht_slot(h, c.tmask);
-                        for (;;) {
-                            const uint32_t y = ht[s];
-                            if (y == HT_EMPTY) break;
-                            if (entry_hub(y) == h) { tk = entry_dist(y); break; }
-                            s = (s + 1) & c.tmask;
-                        }
-                    } else {
-                        const uint32_t *rlab = a.pool + c.koff;
-                        uint32_t lo = 0, hi = c.klen;
-                        while (lo < hi) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
-                        }
-                        if (lo < c.klen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
+            for (int u = 0; u < LU; ++u) {
+                const uint32_t x = x0 + 32 * u + lane;
+                uint32_t j = 0;  // owner: the last candidate whose first entry is <= x
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(FULL, excl, j + step) <= x) j += step;
+                own[u] = j;
+                act[u] = x < total && !((pruned >> j) & 1);
+                ent[u] = act[u] ? a.pool[tc[j].lab_base + x] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                fw[u] = ~0u;  // no filter: every hub goes to the table
+                if (act[u]) {
+                    const TestCand &c = tc[own[u]];
+                    if (c.klen <= FILT_MAX_LEN) {
+                        const uint32_t fb = filt_bit(entry_hub(ent[u]));
+                        fw[u] = a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31);
                     }
-                    p = tk != INF8 && tk + entry_dist(ent) <= level;
                 }
             }
-            pruned |= __reduce_or_sync(FULL, p ? 1u << j : 0u);
+            uint32_t y0[LU];
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                y0[u] = HT_EMPTY;
+                if (act[u] && (fw[u] & 1u)) {
+                    const TestCand &c = tc[own[u]];
+                    if (c.tmask != NONE) y0[u] = a.ht[c.tb + ht_slot(entry_hub(ent[u]), c.tmask)];
+                }
+            }
+            uint32_t pm = 0;  // candidates this step prunes
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                if (!act[u]) continue;
+                ++n_scan;
+                if (!(fw[u] & 1u)) continue;
+                const TestCand &c = tc[own[u]];
+                const uint32_t h = entry_hub(ent[u]);
+                uint32_t tk = INF8;
+                if (c.tmask != NONE) {
+                    const uint32_t *ht = a.ht + c.tb;
+                    uint32_t sl = ht_slot(h, c.tmask), y = y0[u];
+                    for (;;) {
+                        if (y == HT_EMPTY) break;
+                        if (entry_hub(y) == h) { tk = entry_dist(y); break; }
+                        sl = (sl + 1) & c.tmask;
+                        y = ht[sl];
+                    }
+                } else {
+                    const uint32_t *rlab = a.pool + c.koff;
+                    uint32_t lo = 0, hi = c.klen;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < c.klen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
+                }
+                if (tk != INF8 && tk + entry_dist(ent[u]) <= level) pm |= 1u << own[u];
+            }
+            pruned |= __reduce_or_sync(FULL, pm);
         }
         const bool keep = valid && !((pruned >> lane) & 1);
         if (__any_sync(FULL, keep)) {
