@@ -70,6 +70,9 @@ namespace {
 #ifndef LABEL_ROUNDS
 #define LABEL_ROUNDS 4
 #endif
+#ifndef LONG_LABEL_ENTRIES
+#define LONG_LABEL_ENTRIES 64
+#endif
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t HT_EMPTY = 0xffffffffu;
@@ -498,11 +501,13 @@ __global__ void k_batch_clear(BatchArgs a) {
 // candidate j), in two parts:
 //   masks   one candidate with feasible roots at a time: the lanes take the
 //           roots (two each) and compare mask pairs (Sec. 5.3);
-//   labels  the labels L(w) of the candidates the masks did not prune are
-//           laid end to end and the lanes take 32 consecutive entries per
-//           step (lane x's candidate found by a binary search over a warp scan
-//           of the lengths), so short labels do not leave lanes idle and the
-//           chunks of different candidates are in flight together. Each entry
+//   labels  of the candidates the masks did not prune: a long label (at
+//           least LONG_LABEL entries) is scanned by the whole warp, LU rounds
+//           of 32 entries per step; the shorter labels L(w) are laid end to end
+//           and the lanes take LU x 32 consecutive entries per step (lane x's
+//           candidate found by a binary search over a warp scan of the
+//           lengths), so short labels do not leave lanes idle and the chunks
+//           of different candidates are in flight together. Each entry
 //           (h, d) is looked up in the root's filter (roots with labels of at
 //           most FILT_MAX_LEN entries), and only if its bit is set in the
 //           root's hash table T (or, without a table, by a binary search of
@@ -510,6 +515,10 @@ __global__ void k_batch_clear(BatchArgs a) {
 //           pruned takes no further entries.
 // Per-candidate data sits in shared memory for the lanes that work on it.
 constexpr int LU = LABEL_ROUNDS;  // label rounds per step of the test sweep
+// candidates whose labels have at least this many entries are scanned one by
+// one by the whole warp (no owner search per entry, and an exit at the first
+// step that prunes); shorter labels are laid end to end over the lanes
+constexpr uint32_t LONG_LABEL = LONG_LABEL_ENTRIES;
 
 struct TestCand {
     unsigned long long lab_base;  // pool offset of L(w) minus the candidate's first flattened index
@@ -517,6 +526,66 @@ struct TestCand {
     unsigned long long koff;      // L(v_k) in the label pool (binary-search fallback)
     uint32_t slot, tmask, klen, pad;  // tmask = table slots - 1, NONE without a table
 };
+
+// The label test of LU label entries per lane (ent[u], of candidate own[u],
+// where act[u]): in three stages so that the loads of all of them are in
+// flight together -- the filter words, then the first table slot of each hub
+// (collision chains and the binary-search fallback follow one by one). Returns
+// the lane's candidates that an entry prunes (d + T[h] <= level), as bits.
+__device__ __forceinline__ uint32_t lookup_entries(const BatchArgs &a, const TestCand *tc,
+                                                   const uint32_t (&ent)[LU], const uint32_t (&own)[LU],
+                                                   const bool (&act)[LU], uint32_t level, uint32_t &n_scan) {
+    uint32_t fw[LU], y0[LU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        fw[u] = ~0u;  // no filter: every hub goes to the table
+        if (act[u]) {
+            const TestCand &c = tc[own[u]];
+            if (c.klen <= FILT_MAX_LEN) {
+                const uint32_t fb = filt_bit(entry_hub(ent[u]));
+                fw[u] = a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        y0[u] = HT_EMPTY;
+        if (act[u] && (fw[u] & 1u)) {
+            const TestCand &c = tc[own[u]];
+            if (c.tmask != NONE) y0[u] = a.ht[c.tb + ht_slot(entry_hub(ent[u]), c.tmask)];
+        }
+    }
+    uint32_t pm = 0;
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        if (!act[u]) continue;
+        ++n_scan;
+        if (!(fw[u] & 1u)) continue;
+        const TestCand &c = tc[own[u]];
+        const uint32_t h = entry_hub(ent[u]);
+        uint32_t tk = INF8;
+        if (c.tmask != NONE) {
+            const uint32_t *ht = a.ht + c.tb;
+            uint32_t sl = ht_slot(h, c.tmask), y = y0[u];
+            for (;;) {
+                if (y == HT_EMPTY) break;
+                if (entry_hub(y) == h) { tk = entry_dist(y); break; }
+                sl = (sl + 1) & c.tmask;
+                y = ht[sl];
+            }
+        } else {
+            const uint32_t *rlab = a.pool + c.koff;
+            uint32_t lo = 0, hi = c.klen;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
+            }
+            if (lo < c.klen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
+        }
+        if (tk != INF8 && tk + entry_dist(ent[u]) <= level) pm |= 1u << own[u];
+    }
+    return pm;
+}
 
 // The sweep over candidates [b, e) of level `level` by the warps of a grid;
 // tc: this warp's 32 records in shared memory. Adds the label entries it scans
@@ -570,8 +639,10 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
             }
             if (__any_sync(FULL, p)) pruned |= 1u << j;
         }
-        // ---- labels, laid end to end over the unpruned candidates
-        const uint32_t len = (valid && !((pruned >> lane) & 1)) ? wlen : 0;
+        // ---- labels: candidates with long labels get the whole warp in turn;
+        // the labels of the others are laid end to end over the lanes
+        const bool open = valid && !((pruned >> lane) & 1);
+        const uint32_t len = (open && wlen < LONG_LABEL) ? wlen : 0;
         uint32_t incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -593,13 +664,31 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
             tc[lane] = c;
         }
         __syncwarp();
-        // LU rounds of 32 entries per step, in three stages so that the loads of
-        // all rounds are in flight together: the label entries, then the filter
-        // words, then the first table slot of each hub (collision chains and the
-        // binary-search fallback follow one by one)
+        uint32_t ent[LU], own[LU];
+        bool act[LU];
+        // long labels: LU rounds of 32 entries per step, leaving at the first
+        // step that prunes
+        for (uint32_t m = __ballot_sync(FULL, open && wlen >= LONG_LABEL); m; m &= m - 1) {
+            const uint32_t j = __ffs(m) - 1;
+            const uint32_t lj = __shfl_sync(FULL, wlen, j);
+            const unsigned long long base = tc[j].lab_base + __shfl_sync(FULL, excl, j);
+            for (uint32_t x0 = 0; x0 < lj; x0 += 32 * LU) {
+#pragma unroll
+                for (int u = 0; u < LU; ++u) {
+                    const uint32_t x = x0 + 32 * u + lane;
+                    own[u] = j;
+                    act[u] = x < lj;
+                    ent[u] = act[u] ? a.pool[base + x] : 0u;
+                }
+                if (__any_sync(FULL, lookup_entries(a, tc, ent, own, act, level, n_scan) != 0)) {
+                    pruned |= 1u << j;
+                    break;
+                }
+            }
+        }
+        // short labels laid end to end (lane x's candidate found by a binary
+        // search over the warp scan of their lengths)
         for (uint32_t x0 = 0; x0 < total; x0 += 32 * LU) {
-            uint32_t ent[LU], own[LU], fw[LU];
-            bool act[LU];
 #pragma unroll
             for (int u = 0; u < LU; ++u) {
                 const uint32_t x = x0 + 32 * u + lane;
@@ -611,56 +700,7 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
                 act[u] = x < total && !((pruned >> j) & 1);
                 ent[u] = act[u] ? a.pool[tc[j].lab_base + x] : 0u;
             }
-#pragma unroll
-            for (int u = 0; u < LU; ++u) {
-                fw[u] = ~0u;  // no filter: every hub goes to the table
-                if (act[u]) {
-                    const TestCand &c = tc[own[u]];
-                    if (c.klen <= FILT_MAX_LEN) {
-                        const uint32_t fb = filt_bit(entry_hub(ent[u]));
-                        fw[u] = a.filt[(size_t)c.slot * FILT_WORDS + (fb >> 5)] >> (fb & 31);
-                    }
-                }
-            }
-            uint32_t y0[LU];
-#pragma unroll
-            for (int u = 0; u < LU; ++u) {
-                y0[u] = HT_EMPTY;
-                if (act[u] && (fw[u] & 1u)) {
-                    const TestCand &c = tc[own[u]];
-                    if (c.tmask != NONE) y0[u] = a.ht[c.tb + ht_slot(entry_hub(ent[u]), c.tmask)];
-                }
-            }
-            uint32_t pm = 0;  // candidates this step prunes
-#pragma unroll
-            for (int u = 0; u < LU; ++u) {
-                if (!act[u]) continue;
-                ++n_scan;
-                if (!(fw[u] & 1u)) continue;
-                const TestCand &c = tc[own[u]];
-                const uint32_t h = entry_hub(ent[u]);
-                uint32_t tk = INF8;
-                if (c.tmask != NONE) {
-                    const uint32_t *ht = a.ht + c.tb;
-                    uint32_t sl = ht_slot(h, c.tmask), y = y0[u];
-                    for (;;) {
-                        if (y == HT_EMPTY) break;
-                        if (entry_hub(y) == h) { tk = entry_dist(y); break; }
-                        sl = (sl + 1) & c.tmask;
-                        y = ht[sl];
-                    }
-                } else {
-                    const uint32_t *rlab = a.pool + c.koff;
-                    uint32_t lo = 0, hi = c.klen;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (entry_hub(rlab[mid]) < h) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < c.klen && entry_hub(rlab[lo]) == h) tk = entry_dist(rlab[lo]);
-                }
-                if (tk != INF8 && tk + entry_dist(ent[u]) <= level) pm |= 1u << own[u];
-            }
-            pruned |= __reduce_or_sync(FULL, pm);
+            pruned |= __reduce_or_sync(FULL, lookup_entries(a, tc, ent, own, act, level, n_scan));
         }
         const bool keep = valid && !((pruned >> lane) & 1);
         if (__any_sync(FULL, keep)) {
