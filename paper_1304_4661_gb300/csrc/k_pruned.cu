@@ -70,6 +70,9 @@ namespace {
 #ifndef LABEL_ROUNDS
 #define LABEL_ROUNDS 4
 #endif
+#ifndef LABEL_ROUNDS_LOOP
+#define LABEL_ROUNDS_LOOP 2
+#endif
 #ifndef LONG_LABEL_ENTRIES
 #define LONG_LABEL_ENTRIES 64
 #endif
@@ -515,6 +518,8 @@ __global__ void k_batch_clear(BatchArgs a) {
 //           pruned takes no further entries.
 // Per-candidate data sits in shared memory for the lanes that work on it.
 constexpr int LU = LABEL_ROUNDS;  // label rounds per step of the test sweep
+constexpr int LU_LOOP = LABEL_ROUNDS_LOOP;  // the same inside the level loop (fewer
+                                            // registers: the loop's own state is live)
 // candidates whose labels have at least this many entries are scanned one by
 // one by the whole warp (no owner search per entry, and an exit at the first
 // step that prunes); shorter labels are laid end to end over the lanes
@@ -532,12 +537,13 @@ struct TestCand {
 // flight together -- the filter words, then the first table slot of each hub
 // (collision chains and the binary-search fallback follow one by one). Returns
 // the lane's candidates that an entry prunes (d + T[h] <= level), as bits.
+template <int U>
 __device__ __forceinline__ uint32_t lookup_entries(const BatchArgs &a, const TestCand *tc,
-                                                   const uint32_t (&ent)[LU], const uint32_t (&own)[LU],
-                                                   const bool (&act)[LU], uint32_t level, uint32_t &n_scan) {
-    uint32_t fw[LU], y0[LU];
+                                                   const uint32_t (&ent)[U], const uint32_t (&own)[U],
+                                                   const bool (&act)[U], uint32_t level, uint32_t &n_scan) {
+    uint32_t fw[U], y0[U];
 #pragma unroll
-    for (int u = 0; u < LU; ++u) {
+    for (int u = 0; u < U; ++u) {
         fw[u] = ~0u;  // no filter: every hub goes to the table
         if (act[u]) {
             const TestCand &c = tc[own[u]];
@@ -548,7 +554,7 @@ __device__ __forceinline__ uint32_t lookup_entries(const BatchArgs &a, const Tes
         }
     }
 #pragma unroll
-    for (int u = 0; u < LU; ++u) {
+    for (int u = 0; u < U; ++u) {
         y0[u] = HT_EMPTY;
         if (act[u] && (fw[u] & 1u)) {
             const TestCand &c = tc[own[u]];
@@ -557,7 +563,7 @@ __device__ __forceinline__ uint32_t lookup_entries(const BatchArgs &a, const Tes
     }
     uint32_t pm = 0;
 #pragma unroll
-    for (int u = 0; u < LU; ++u) {
+    for (int u = 0; u < U; ++u) {
         if (!act[u]) continue;
         ++n_scan;
         if (!(fw[u] & 1u)) continue;
@@ -590,6 +596,7 @@ __device__ __forceinline__ uint32_t lookup_entries(const BatchArgs &a, const Tes
 // The sweep over candidates [b, e) of level `level` by the warps of a grid;
 // tc: this warp's 32 records in shared memory. Adds the label entries it scans
 // and the mask pairs it reads to n_scan / n_mask.
+template <int U>
 __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long b, unsigned long long e,
                                           uint32_t level, TestCand *tc, uint32_t &n_scan, uint32_t &n_mask) {
     const int lane = threadIdx.x & 31;
@@ -664,17 +671,17 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
             tc[lane] = c;
         }
         __syncwarp();
-        uint32_t ent[LU], own[LU];
-        bool act[LU];
+        uint32_t ent[U], own[U];
+        bool act[U];
         // long labels: LU rounds of 32 entries per step, leaving at the first
         // step that prunes
         for (uint32_t m = __ballot_sync(FULL, open && wlen >= LONG_LABEL); m; m &= m - 1) {
             const uint32_t j = __ffs(m) - 1;
             const uint32_t lj = __shfl_sync(FULL, wlen, j);
             const unsigned long long base = tc[j].lab_base + __shfl_sync(FULL, excl, j);
-            for (uint32_t x0 = 0; x0 < lj; x0 += 32 * LU) {
+            for (uint32_t x0 = 0; x0 < lj; x0 += 32 * U) {
 #pragma unroll
-                for (int u = 0; u < LU; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const uint32_t x = x0 + 32 * u + lane;
                     own[u] = j;
                     act[u] = x < lj;
@@ -688,9 +695,9 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
         }
         // short labels laid end to end (lane x's candidate found by a binary
         // search over the warp scan of their lengths)
-        for (uint32_t x0 = 0; x0 < total; x0 += 32 * LU) {
+        for (uint32_t x0 = 0; x0 < total; x0 += 32 * U) {
 #pragma unroll
-            for (int u = 0; u < LU; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const uint32_t x = x0 + 32 * u + lane;
                 uint32_t j = 0;  // owner: the last candidate whose first entry is <= x
 #pragma unroll
@@ -717,7 +724,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_test(BatchArgs a) {
     __shared__ TestCand s_cand[BLOCK / 32][32];
     uint32_t n_scan = 0, n_mask = 0;
-    test_body(a, a.desc->cand_b, a.desc->cand_e, a.desc->level + 1, s_cand[threadIdx.x >> 5], n_scan, n_mask);
+    test_body<LU>(a, a.desc->cand_b, a.desc->cand_e, a.desc->level + 1, s_cand[threadIdx.x >> 5], n_scan, n_mask);
     flush_work(a, 0, n_scan, n_mask);
 }
 
@@ -791,7 +798,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_levels(BatchArgs 
         const unsigned long long cand_b = cand_e;
         const unsigned long long cn = *(volatile unsigned long long *)&ls->cand_n;
         cand_e = cn < a.cand_cap ? cn : a.cand_cap;
-        test_body(a, cand_b, cand_e, level + 1, tc, n_scan, n_mask);
+        test_body<LU_LOOP>(a, cand_b, cand_e, level + 1, tc, n_scan, n_mask);
         if (!grid_barrier(a, ls)) break;
         if (timer) {
             const unsigned long long t2 = global_ns();
