@@ -190,23 +190,26 @@ __device__ __forceinline__ void store_answer(const QueryArgs &a, uint64_t qi, ui
     }
 }
 
-// One warp per pair, 32 pairs at a time: lane j first fetches pair j's ids,
-// ranks and label offsets (three dependent loads, now in flight for 32 pairs
+// One warp per pair, PG pairs at a time: lane j < PG first fetches pair j's
+// ids, ranks and label offsets (three dependent loads, in flight for PG pairs
 // at once instead of one after another), and answers the trivial pairs; the
-// warp then answers the others one by one from the lanes' registers. Eight
-// CTAs per SM (32 registers a thread): the kernel is bound by the latency of
-// its loads, so it wants every resident warp it can get.
+// warp then answers the others one by one from the lanes' registers. PG is
+// 32 for launches that fill the GPU that way and smaller for launches that
+// would otherwise leave warps idle. Eight CTAs per SM (32 registers a
+// thread): the kernel is bound by the latency of its loads, so it wants every
+// resident warp it can get.
+template <int PG>
 __global__ void __launch_bounds__(256, 8) k_query(QueryArgs a) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; q0 < a.q;
-         q0 += warps * 32) {
+    for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PG; q0 < a.q;
+         q0 += warps * PG) {
         const uint64_t qi = q0 + lane;
         uint32_t s = 0, t = 0, ans = 0;
         bool bad = false, open = false;
         uint64_t os = 0, ot = 0;
         uint32_t ls = 0, lt = 0;
-        if (qi < a.q) {
+        if (lane < PG && qi < a.q) {
             open = !trivial_pair(a, a.src[qi * a.stride], a.dst[qi * a.stride], &s, &t, &ans, &bad);
             if (open) {
                 os = a.lab_off[s];
@@ -285,7 +288,7 @@ int query_launch_strided(const pll_index *ix, const uint32_t *d_src, const uint3
     if (res == 0) {
         int sms = 0, per = 0;
         PLL_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        PLL_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query, 256, 0));
+        PLL_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query<32>, 256, 0));
         res = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
         if (dev < 64) resident[dev].store(res, std::memory_order_relaxed);
     }
@@ -302,8 +305,13 @@ int query_launch_strided(const pll_index *ix, const uint32_t *d_src, const uint3
     } else if (q <= 4 * R) {
         k_query_wide<2><<<(unsigned)((q + 3) / 4), 256, 0, s>>>(a);
     } else {
-        const uint64_t want = (q + 255) / 256;  // a block takes 8 groups of 32 pairs per step
-        k_query<<<(unsigned)(want < R ? want : R), 256, 0, s>>>(a);
+        // pairs per warp group: as many as keep every resident warp busy (R
+        // blocks of 8 warps), up to 32
+        const uint64_t per = q / (R * 8);
+        if (per >= 32) k_query<32><<<(unsigned)R, 256, 0, s>>>(a);
+        else if (per >= 8) k_query<8><<<(unsigned)R, 256, 0, s>>>(a);
+        else if (per >= 2) k_query<2><<<(unsigned)R, 256, 0, s>>>(a);
+        else k_query<1><<<(unsigned)R, 256, 0, s>>>(a);
     }
     PLL_TRY(cudaGetLastError());
     return PLL_OK;
