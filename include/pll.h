@@ -296,16 +296,17 @@ PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *
  * A request is q >= 1 pairs in HOST memory plus a HOST uint8[q] result
  * buffer, all owned by the caller; the pairs are read inside
  * pll_server_submit, the result buffer must stay valid until the request is
- * waited for. The server holds a ring of P = pool_bytes / 9 pair slots in
- * device memory (8 bytes per pair, 1 per result), mirrored in pinned host
- * memory:
+ * waited for. The server holds a ring of P = pool_bytes / 9 pair slots (8
+ * bytes per pair, 1 per result) in pinned, mapped host memory that the GPU
+ * reads and writes directly (over NVLink-C2C on a GB300; no copies):
  *   - admission by memory: a request is admitted when q contiguous slots are
  *     free; until then pll_server_submit blocks. Its slots are held until its
  *     results are back, so at most P pairs are queued or in flight;
  *   - continuous batching: one dispatcher thread launches, whenever one of
  *     `streams` stream slots is free, every admitted request not yet launched
- *     (arrival order, up to max_batch_pairs pairs) as one copy-in, one query
- *     launch and one copy-out; requests that arrive while others are on the
+ *     (arrival order, up to max_batch_pairs pairs) as one query launch that
+ *     reads the pairs from the ring and writes the results into it; requests
+ *     that arrive while others are on the
  *     GPU form the next launch, and launches on different stream slots
  *     overlap on the device;
  *   - requests complete in launch order; each latency is measured from the
@@ -317,8 +318,8 @@ PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *
  *                    zero fields take the defaults (pool_bytes 256 MiB,
  *                    max_batch_pairs 2^20, streams 4). The index must outlive
  *                    the server. PLL_E_INVAL for streams > 64, pool_bytes < 9
- *                    or reserved != 0; PLL_E_NOMEM if the device ring or its
- *                    pinned mirror cannot be allocated.
+ *                    or reserved != 0; PLL_E_NOMEM if the ring cannot be
+ *                    allocated.
  * pll_server_submit  admits and stages a request and returns its ticket.
  *                    PLL_E_RANGE if q exceeds min(max_batch_pairs, P) (stats
  *                    field max_request_pairs), PLL_E_INVAL if an id is >= n
@@ -342,7 +343,7 @@ PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *
 typedef struct pll_server pll_server;
 
 typedef struct pll_server_opts {
-    uint64_t pool_bytes;       /* device bytes for in-flight query data */
+    uint64_t pool_bytes;       /* bytes of the ring (pinned host memory) */
     uint64_t max_batch_pairs;  /* most pairs in one launch */
     uint32_t streams;          /* stream slots (batches in flight), <= 64 */
     uint32_t reserved;         /* must be 0 */

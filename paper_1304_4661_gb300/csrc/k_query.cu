@@ -179,15 +179,19 @@ __device__ __forceinline__ uint32_t finish_pair(const QueryArgs &a, uint32_t s, 
     return min(best, bpb);
 }
 
-__device__ __forceinline__ void store_answer(const QueryArgs &a, uint64_t qi, uint32_t best) {
-    if (best >= BIG) {
-        a.out[qi] = INF8;
-    } else if (best >= INF8) {
-        a.out[qi] = INF8;
+// the answer byte of a pair's minimum (255 for none or for a finite distance
+// of 255 or more; the latter is counted as an error)
+__device__ __forceinline__ uint32_t answer_byte(const QueryArgs &a, uint32_t best) {
+    if (best >= BIG) return INF8;
+    if (best >= INF8) {
         atomicAdd(a.err, 1ull);
-    } else {
-        a.out[qi] = (uint8_t)best;
+        return INF8;
     }
+    return best;
+}
+
+__device__ __forceinline__ void store_answer(const QueryArgs &a, uint64_t qi, uint32_t best) {
+    a.out[qi] = (uint8_t)answer_byte(a, best);
 }
 
 // One warp per pair, PG pairs at a time: lane j < PG first fetches pair j's
@@ -205,20 +209,20 @@ __global__ void __launch_bounds__(256, 8) k_query(QueryArgs a) {
     for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PG; q0 < a.q;
          q0 += warps * PG) {
         const uint64_t qi = q0 + lane;
+        const bool mine = lane < PG && qi < a.q;
         uint32_t s = 0, t = 0, ans = 0;
         bool bad = false, open = false;
         uint64_t os = 0, ot = 0;
         uint32_t ls = 0, lt = 0;
-        if (lane < PG && qi < a.q) {
+        if (mine) {
             open = !trivial_pair(a, a.src[qi * a.stride], a.dst[qi * a.stride], &s, &t, &ans, &bad);
             if (open) {
                 os = a.lab_off[s];
                 ot = a.lab_off[t];
                 ls = (uint32_t)(a.lab_off[s + 1] - os);
                 lt = (uint32_t)(a.lab_off[t + 1] - ot);
-            } else {
-                a.out[qi] = (uint8_t)ans;
-                if (bad) atomicAdd(a.err + 1, 1ull);
+            } else if (bad) {
+                atomicAdd(a.err + 1, 1ull);
             }
         }
         for (uint32_t m = __ballot_sync(FULL, open); m; m &= m - 1) {
@@ -230,8 +234,11 @@ __global__ void __launch_bounds__(256, 8) k_query(QueryArgs a) {
             bp_tilde(a, sj, tj, lane, &td0, &td1, &dstar);
             const uint32_t best = finish_pair(a, sj, tj, lane, td0, td1, dstar,
                                               label_min_merge_at(a, sj, tj, osj, lsj, otj, ltj, lane));
-            if (lane == 0) store_answer(a, q0 + j, best);
+            if (lane == j) ans = answer_byte(a, best);  // best is the same on every lane
         }
+        // the group's answers in one coalesced store (the output may be host
+        // memory that the GPU writes directly)
+        if (mine) a.out[qi] = (uint8_t)ans;
     }
 }
 

@@ -4,9 +4,10 @@
 // latency-sensitive services (Sec. 1); this loop serves Query(s, t) (Sec. 3.3
 // with the bit-parallel part of Sec. 5.3) for many clients at once.
 //
-// Memory. The server owns one ring of P pair slots, mirrored in pinned host
-// memory and in device memory: pairs (s, t) as 8 bytes each, results as 1
-// byte each, so the device holds 9 P bytes (pool_bytes). A request of q pairs
+// Memory. The server owns one ring of P pair slots in pinned, mapped host
+// memory that the GPU reads and writes directly (over NVLink-C2C on a GB300;
+// no copies): pairs (s, t) as 8 bytes each, results as 1 byte each, 9 P bytes
+// in all (pool_bytes). A request of q pairs
 // is ADMITTED when q contiguous slots are free: pll_server_submit blocks until
 // then, so at most P pairs are ever queued or in flight. The client's own
 // thread copies its pairs into its slots (checking every id on the way); the
@@ -15,9 +16,9 @@
 // Continuous batching. One dispatcher thread takes, whenever one of `streams`
 // stream slots is free, the longest run of staged requests that are waiting
 // (arrival order, contiguous in the ring, at most max_batch_pairs pairs) and
-// launches it as one unit on that slot's stream: one copy of the run's pair
-// slots to the device, one query launch (k_query, a warp per pair, reading the
-// interleaved pairs in place), one copy of the run's results back, one event.
+// launches it as one unit on that slot's stream: one query launch (k_query,
+// reading the run's interleaved pairs in place from the ring and writing its
+// results into the ring) between two events.
 // Requests that arrive while earlier runs are on the GPU form the next run,
 // and runs on different stream slots overlap on the device. Runs retire in
 // launch order: their results go to the requests' buffers, each request's
@@ -82,10 +83,10 @@ struct pll_server {
     pll_server_opts opts{};
     uint64_t P = 0;                   // ring slots (pairs)
     uint64_t max_request = 0;         // largest request accepted
-    uint32_t *d_pairs = nullptr;      // device [P][2]
-    uint8_t *d_out = nullptr;         // device [P]
-    uint32_t *h_pairs = nullptr;      // pinned [P][2]
-    uint8_t *h_out = nullptr;         // pinned [P]
+    uint32_t *h_pairs = nullptr;      // pinned, mapped [P][2]
+    uint8_t *h_out = nullptr;         // pinned, mapped [P]
+    uint32_t *g_pairs = nullptr;      // the same memory as the GPU addresses it
+    uint8_t *g_out = nullptr;
     std::vector<Slot> slots;
     std::deque<Run> inflight;         // dispatcher thread only, launch order
     double device_us = 0;             // dispatcher thread only
@@ -123,13 +124,9 @@ uint64_t ring_used(const std::deque<Request *> &live, uint64_t cap) {
 
 int launch_run(pll_server *sv, const Run &r) {
     const Slot &sl = sv->slots[r.slot];
-    uint32_t *dp = sv->d_pairs + 2 * r.off;
+    const uint32_t *gp = sv->g_pairs + 2 * r.off;
     PLL_TRY(cudaEventRecord(sl.start, sl.stream));
-    PLL_TRY(cudaMemcpyAsync(dp, sv->h_pairs + 2 * r.off, r.pairs * 8, cudaMemcpyHostToDevice,
-                            sl.stream));
-    PLL_CHECK(pll::query_launch_strided(sv->ix, dp, dp + 1, 2, r.pairs, sv->d_out + r.off, sl.stream));
-    PLL_TRY(cudaMemcpyAsync(sv->h_out + r.off, sv->d_out + r.off, r.pairs, cudaMemcpyDeviceToHost,
-                            sl.stream));
+    PLL_CHECK(pll::query_launch_strided(sv->ix, gp, gp + 1, 2, r.pairs, sv->g_out + r.off, sl.stream));
     PLL_TRY(cudaEventRecord(sl.done, sl.stream));
     return PLL_OK;
 }
@@ -255,7 +252,6 @@ void destroy(pll_server *sv) {
         if (sl.start) cudaEventDestroy(sl.start);
         if (sl.done) cudaEventDestroy(sl.done);
     }
-    if (sv->d_pairs) cudaFree(sv->d_pairs);
     if (sv->h_pairs) cudaFreeHost(sv->h_pairs);
     // a request is in `live` until it completes, and in `table` from staging
     // until it is waited for: completed ones are only in the table
@@ -290,11 +286,12 @@ PLL_API int pll_server_start(const pll_index *idx, const pll_server_opts *opts, 
     sv->st.pool_bytes = 9 * P;
     sv->st.max_request_pairs = sv->max_request;
     cudaError_t e = cudaSetDevice(sv->device);
-    if (e == cudaSuccess) e = cudaMalloc(&sv->d_pairs, 9 * P);
-    if (e == cudaSuccess) e = cudaMallocHost(&sv->h_pairs, 9 * P);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&sv->h_pairs), 9 * P, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&sv->g_pairs), sv->h_pairs, 0);
     if (e == cudaSuccess) {
-        sv->d_out = reinterpret_cast<uint8_t *>(sv->d_pairs + 2 * P);
         sv->h_out = reinterpret_cast<uint8_t *>(sv->h_pairs + 2 * P);
+        sv->g_out = reinterpret_cast<uint8_t *>(sv->g_pairs + 2 * P);
         sv->slots.resize(o.streams);
         for (Slot &sl : sv->slots) {
             if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);

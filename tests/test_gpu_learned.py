@@ -187,6 +187,11 @@ def test_learned_order_trains_and_builds_exact_labels():
     learned = ix.label_entries()
     print(f"label entries: learned {learned}, degree {deg_entries}, random {rnd_entries}")
     assert learned < rnd_entries / 2
-    assert learned < 1.5 * deg_entries
+    # The network is trained to predict the labels each vertex hubs under the
+    # Degree order; ordering by that cannot beat the Degree order itself (even
+    # the exact hub counts give 0.2-0.3 % more entries on R-MAT 13-15). Here it
+    # gives 21,416 entries against Degree's 21,113 (1.4 % more; training is
+    # deterministic): a regression past 2.5 % fails.
+    assert learned <= 1.025 * deg_entries
     s, u = gg.pairs(g.n, 20000, 4)
     assert np.array_equal(ix.query(dev_u32(s), dev_u32(u)).cpu().numpy(), ref.query_batch(s, u))
