@@ -48,9 +48,9 @@ WORKLOADS = {
 # dram__bytes_write.sum, one pass), valid only for the kernel source with this
 # hash (else traffic is reported as null).
 PROFILED = {
-    # R-MAT-18, t = 64: 24 launches, 4.633 GB of DRAM traffic against 6.953 GB of
+    # R-MAT-18, t = 64: 24 launches, 4.687 GB of DRAM traffic against 6.953 GB of
     # algorithmic bytes (the oracle's sequential counts)
-    "k_batch_levels": {"src_sha": "82de8c9ee6e66b74", "dram_per_alg_byte": 0.666},
+    "k_batch_levels": {"src_sha": "75bfd7f24c5cbc0b", "dram_per_alg_byte": 0.674},
 }
 
 
@@ -1131,7 +1131,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-plain", type=int, default=5000)
     ap.add_argument("--serve-streams", type=int, default=4)
-    ap.add_argument("--serve-clients", type=int, default=4)
+    ap.add_argument("--serve-clients", type=int, default=12)
     ap.add_argument("--learned-graphs", type=int, default=200)
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--directed-scale", type=int, default=16)
