@@ -355,10 +355,21 @@ def run_ours(args, w, ws, rank, local):
         unit_src = "GPU counters"
     # expand: a labelled vertex's neighbour ids (4 per arc) and its entry (4 + 1);
     # a dequeued vertex's offsets (8) and bit-parallel distance row (t bytes)
-    exp_bytes = 4 * units["labeled_deg"] + 5 * units["labeled"] + (8 + t) * units["visited"]
+    def expand_bytes(u):
+        return 4 * u["labeled_deg"] + 5 * u["labeled"] + (8 + t) * u["visited"]
+
     # test: the label entries its prune tests scan (4 bytes each); mask bytes
     # are not counted (the distance filter of Sec. 5.3 leaves most unread)
-    test_bytes = 4 * units["scanned"]
+    def test_bytes_of(u):
+        return 4 * u["scanned"]
+
+    exp_bytes = expand_bytes(units)
+    test_bytes = test_bytes_of(units)
+    # the same per-unit bytes over the GPU's own work counts (its root batches'
+    # surplus included; a vertex that the bit-parallel bound prunes is counted
+    # each time it is reached), for comparison with the sequential-count figure
+    gpu_units = {"visited": st["visited"], "labeled": st["pre_cleanup"],
+                 "scanned": st["pruned_scanned"], "labeled_deg": st["pruned_expanded"]}
     # per pair: ids (8), ranks (8), 2 x t distance bytes, 4 label offsets (32),
     # the result byte, and both labels (4 bytes per entry; Lsz is by vertex id)
     q_bytes = q * (8 + 8 + 2 * t + 32 + 1) + 4 * int(Lsz[s].sum() + Lsz[u].sum())
@@ -408,6 +419,11 @@ def run_ours(args, w, ws, rank, local):
                 "phases": {k: {"ms_per_step": round(v["ms_per_step"], 3),
                                "achieved_gbs": round(v["bytes"] / max(v["ms_per_step"], 1e-9) / 1e6, 1)}
                            for k, v in phases.items()}}
+    if dom == "k_batch_levels" and seq:
+        gb = expand_bytes(gpu_units) + test_bytes_of(gpu_units)
+        ga = gb / max(kd["ms_per_step"], 1e-9) / 1e6
+        roofline["with_gpu_counts"] = {"achieved": round(ga, 1), "frac": round(ga / hbm, 4),
+                                       "algorithmic_bytes_per_launch": round(gb / kd["launches"])}
 
     out = {
         "metric": METRIC, "value": round(build_ms / 1e3, 6), "unit": "s", "n_gpus": ws,
