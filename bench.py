@@ -1154,9 +1154,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--host-levels", action="store_true",
                     help="run each root batch's levels as separate launches (PLL_BUILD_HOST_LEVELS)")
+    ap.add_argument("--graph-levels", action="store_true",
+                    help="run each root batch's levels as one CUDA graph launch (PLL_BUILD_GRAPH_LEVELS)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    args.flags = 1 if args.host_levels else 0  # PLL_BUILD_HOST_LEVELS
+    args.flags = (1 if args.host_levels else 0) | (2 if args.graph_levels else 0)  # PLL_BUILD_*_LEVELS
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload in ("batch256", "serve", "learned", "variants", "paths", "directed"):

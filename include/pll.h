@@ -72,6 +72,11 @@ typedef struct pll_index pll_index;
  * Same labels either way; also taken when the device cannot launch
  * cooperatively. */
 #define PLL_BUILD_HOST_LEVELS 1u
+/* pll_build_opts.flags: the levels of each root batch run as one CUDA graph
+ * launch, a conditional while node over the expand and test sweeps (separate
+ * kernels) that a device-side step stops when the frontier is empty. Same
+ * labels; PLL_BUILD_HOST_LEVELS takes precedence. */
+#define PLL_BUILD_GRAPH_LEVELS 2u
 
 typedef struct pll_build_opts {
     uint32_t t;          /* bit-parallel roots, 0..PLL_MAX_T (Sec. 5.4). */
@@ -82,7 +87,7 @@ typedef struct pll_build_opts {
                             gives the same labels. */
     uint32_t block;      /* threads per CTA of the pruned-BFS kernel: 128,
                             256, 512 or 1024; 0 = library default (256). */
-    uint32_t flags;      /* 0, or PLL_BUILD_HOST_LEVELS. */
+    uint32_t flags;      /* 0, PLL_BUILD_HOST_LEVELS or PLL_BUILD_GRAPH_LEVELS. */
     uint64_t reserved;   /* must be 0. */
 } pll_build_opts;
 

@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_levels(BatchArgs 
 }
 
 // descriptor steps between sweeps (one thread)
-__global__ void k_batch_advance(BatchArgs a, int phase) {
+__device__ __forceinline__ void advance_desc(const BatchArgs &a, int phase) {
     LevelDesc *d = a.desc;
     const unsigned long long cn = a.ctr->cand_n, on = a.ctr->out_n;
     if (phase == 0) {          // after init: level 0 = the roots
@@ -831,6 +831,7 @@ __global__ void k_batch_advance(BatchArgs a, int phase) {
         d->level = 0;
         d->cand_b = 0;
         d->cand_e = 0;
+        if (a.loop) a.loop->t_mark = global_ns();
     } else if (phase == 1) {   // after expand: candidates of level + 1
         d->cand_b = d->cand_e;
         d->cand_e = cn < a.cand_cap ? cn : a.cand_cap;
@@ -839,6 +840,64 @@ __global__ void k_batch_advance(BatchArgs a, int phase) {
         d->lvl_e = on < a.out_cap ? on : a.out_cap;
         d->level += 1;
     }
+}
+
+__global__ void k_batch_advance(BatchArgs a, int phase) { advance_desc(a, phase); }
+
+// ---- the level loop as a CUDA graph: a while node whose body is expand,
+// advance(1), test, advance(2); the second advance sets the loop condition.
+// The kernels read the batch's arguments from device memory (the host writes
+// them before each launch of the graph), so one instantiated graph serves
+// every batch of a build.
+// the batch's arguments, copied once per CTA from device memory into shared
+// memory (read there as cheaply as kernel parameters)
+__device__ __forceinline__ const BatchArgs &args_to_shared(const BatchArgs *ap, BatchArgs *sa) {
+    static_assert(sizeof(BatchArgs) % 8 == 0, "BatchArgs is copied in 8-byte words");
+    constexpr unsigned W = sizeof(BatchArgs) / 8;
+    for (unsigned i = threadIdx.x; i < W; i += blockDim.x)
+        reinterpret_cast<uint64_t *>(sa)[i] = reinterpret_cast<const uint64_t *>(ap)[i];
+    __syncthreads();
+    return *sa;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_expand_g(const BatchArgs *__restrict__ ap) {
+    extern __shared__ uint4 s_rows[];
+    __shared__ BatchArgs s_args;
+    const BatchArgs &a = args_to_shared(ap, &s_args);
+    uint32_t nexp = 0, nreach = 0;
+    expand_body(a, a.desc->lvl_b, a.desc->lvl_e, a.desc->level,
+                s_rows + (size_t)(threadIdx.x >> 5) * (PLL_MAX_T / 16), nexp, nreach);
+    flush_work(a, 2, nexp, nreach);
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_batch_test_g(const BatchArgs *__restrict__ ap) {
+    __shared__ TestCand s_cand[BLOCK / 32][32];
+    __shared__ BatchArgs s_args;
+    const BatchArgs &a = args_to_shared(ap, &s_args);
+    uint32_t n_scan = 0, n_mask = 0;
+    test_body<LU>(a, a.desc->cand_b, a.desc->cand_e, a.desc->level + 1, s_cand[threadIdx.x >> 5], n_scan, n_mask);
+    flush_work(a, 0, n_scan, n_mask);
+}
+
+// phase 1 / 2 of advance_desc, plus the phases' wall times; phase 2 sets the
+// loop's condition: another level while the frontier is not empty and no
+// buffer overflowed and no depth reached 255
+__global__ void k_batch_advance_g(const BatchArgs *__restrict__ ap, int phase, cudaGraphConditionalHandle h) {
+    const BatchArgs &a = *ap;
+    advance_desc(a, phase);
+    LoopState *ls = a.loop;
+    const unsigned long long now = global_ns();
+    if (phase == 1) {
+        ls->ns_expand += now - ls->t_mark;
+    } else {
+        ls->ns_test += now - ls->t_mark;
+        ls->levels += 1;
+        const bool more = a.desc->lvl_b < a.desc->lvl_e && !(a.ctr->err & (ERR_DEPTH | ERR_BUF));
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+    ls->t_mark = now;
 }
 
 }  // namespace
@@ -965,6 +1024,72 @@ int batch_levels(const BatchArgs &a, uint32_t block, int grid, cudaStream_t s) {
     }
     PLL_TRY(e);
     return PLL_OK;
+}
+
+template <int BLOCK>
+static int graph_build(const int *grid, const BatchArgs *d_args, cudaGraph_t *pg, cudaGraphExec_t *pexec) {
+    cudaGraph_t g = nullptr;
+    PLL_TRY(cudaGraphCreate(&g, 0));
+    struct Guard {
+        cudaGraph_t g;
+        ~Guard() { if (g) cudaGraphDestroy(g); }
+    } guard{g};
+    PLL_TRY(cudaFuncSetAttribute(k_batch_expand_g<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)expand_smem<BLOCK>()));
+    cudaGraphConditionalHandle h;
+    PLL_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    PLL_TRY(cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const BatchArgs *ap = d_args;
+    int ph1 = 1, ph2 = 2;
+    void *a_exp[] = {&ap};
+    void *a_adv1[] = {&ap, &ph1, &h};
+    void *a_tst[] = {&ap};
+    void *a_adv2[] = {&ap, &ph2, &h};
+    cudaKernelNodeParams kp{};
+    cudaGraphNode_t n[4];
+    kp.func = reinterpret_cast<void *>(k_batch_expand_g<BLOCK>);
+    kp.gridDim = dim3(grid[0]);
+    kp.blockDim = dim3(BLOCK);
+    kp.sharedMemBytes = (unsigned)expand_smem<BLOCK>();
+    kp.kernelParams = a_exp;
+    PLL_TRY(cudaGraphAddKernelNode(&n[0], body, nullptr, 0, &kp));
+    kp.func = reinterpret_cast<void *>(k_batch_advance_g);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = a_adv1;
+    PLL_TRY(cudaGraphAddKernelNode(&n[1], body, &n[0], 1, &kp));
+    kp.func = reinterpret_cast<void *>(k_batch_test_g<BLOCK>);
+    kp.gridDim = dim3(grid[1]);
+    kp.blockDim = dim3(BLOCK);
+    kp.kernelParams = a_tst;
+    PLL_TRY(cudaGraphAddKernelNode(&n[2], body, &n[1], 1, &kp));
+    kp.func = reinterpret_cast<void *>(k_batch_advance_g);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = a_adv2;
+    PLL_TRY(cudaGraphAddKernelNode(&n[3], body, &n[2], 1, &kp));
+    PLL_TRY(cudaGraphInstantiate(pexec, g, 0));
+    *pg = g;
+    guard.g = nullptr;
+    return PLL_OK;
+}
+
+int batch_graph_build(uint32_t block, const int *grid, const BatchArgs *d_args, cudaGraph_t *g,
+                      cudaGraphExec_t *exec) {
+    switch (block) {
+        case 128: return graph_build<128>(grid, d_args, g, exec);
+        case 512: return graph_build<512>(grid, d_args, g, exec);
+        case 1024: return graph_build<1024>(grid, d_args, g, exec);
+        default: return graph_build<256>(grid, d_args, g, exec);
+    }
 }
 
 // ev: null, or four events recorded around the expand and test sweeps

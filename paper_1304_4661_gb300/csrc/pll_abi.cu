@@ -92,7 +92,9 @@ struct Timer {
 
 // Step 3: batched pruned BFS + cleanup + append, then step 4.
 int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, const uint8_t *inX,
-                 uint32_t bmax, uint32_t block, bool host_levels, cudaStream_t s) {
+                 uint32_t bmax, uint32_t block, uint32_t flags, cudaStream_t s) {
+    const bool host_levels = (flags & PLL_BUILD_HOST_LEVELS) != 0;
+    const bool graph_levels = !host_levels && (flags & PLL_BUILD_GRAPH_LEVELS) != 0;
     const uint32_t n = ix->n;
     LabelStore st;
     st.n = n;
@@ -128,7 +130,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     // enqueues the levels itself when asked to, or when the device cannot
     // launch cooperatively)
     int lgrid = 0;
-    if (!host_levels) PLL_CHECK(batch_levels_grid(block, &lgrid));
+    if (!host_levels && !graph_levels) PLL_CHECK(batch_levels_grid(block, &lgrid));
     const bool device_levels = lgrid > 0;
     DevMem m_loop;
     PLL_CHECK(m_loop.alloc(sizeof(LoopState)));
@@ -181,6 +183,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     struct Mirror {
         BatchCounters c;
         LevelDesc d;
+        BatchArgs args;  // staging of the graph loop's device-side arguments
     };
     Mirror *h = nullptr;
     PLL_TRY(host_malloc(&h, sizeof(Mirror)));
@@ -208,6 +211,24 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             for (int i = 0; i < 16; ++i) if (sw[i]) cudaEventDestroy(sw[i]);
         }
     } ev_guard{ev0, ev1, sweep_ev};
+
+    // the level loop as a CUDA graph (PLL_BUILD_GRAPH_LEVELS): instantiated
+    // once, launched per batch after the batch's arguments are copied in
+    DevMem m_args;
+    cudaGraph_t lgraph = nullptr;
+    cudaGraphExec_t lexec = nullptr;
+    struct GraphGuard {
+        cudaGraph_t *g;
+        cudaGraphExec_t *e;
+        ~GraphGuard() {
+            if (*e) cudaGraphExecDestroy(*e);
+            if (*g) cudaGraphDestroy(*g);
+        }
+    } graph_guard{&lgraph, &lexec};
+    if (graph_levels) {
+        PLL_CHECK(m_args.alloc(sizeof(BatchArgs)));
+        PLL_CHECK(batch_graph_build(block, grid, m_args.as<BatchArgs>(), &lgraph, &lexec));
+    }
 
     uint64_t total = 0, pre = 0, batches = 0;
     uint32_t k0 = 0, B = std::min<uint32_t>(64, bmax);
@@ -258,11 +279,19 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             PLL_TRY(cudaEventRecord(sweep_ev[1], s));
             ix->stats.launches += 1;
             ix->stats.levels_launches += 1;
+        } else if (graph_levels) {
+            // every level of the batch in one graph launch (a while node)
+            h->args = a;
+            PLL_TRY(cudaMemcpyAsync(m_args.p, &h->args, sizeof(BatchArgs), cudaMemcpyHostToDevice, s));
+            PLL_TRY(cudaEventRecord(sweep_ev[0], s));
+            PLL_TRY(cudaGraphLaunch(lexec, s));
+            PLL_TRY(cudaEventRecord(sweep_ev[1], s));
+            ix->stats.levels_launches += 1;
         }
         // or: enqueue levels ahead; read back only to find the empty frontier.
         // Events around every expand and test sweep give their device times.
         uint32_t ahead = 4;
-        for (; !device_levels;) {
+        for (; !device_levels && !graph_levels;) {
             for (uint32_t l = 0; l < ahead; ++l)
                 PLL_CHECK(batch_level(a, grid, block, s, sweep_ev + 4 * l));
             ix->stats.launches += 4ull * ahead;
@@ -291,7 +320,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             PLL_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
             ix->stats.ms_pruned_kernel += ms;
             ix->stats.pruned_launches += 1;
-            if (device_levels) {
+            if (device_levels || graph_levels) {
                 PLL_TRY(cudaEventElapsedTime(&ms, sweep_ev[0], sweep_ev[1]));
                 ix->stats.ms_levels += ms;
             }
@@ -362,7 +391,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         k0 = k1;
         B = std::min<uint32_t>(B * 2, bmax);
     }
-    if (device_levels) {  // phase times and level counts of the device-side loop
+    if (device_levels || graph_levels) {  // phase times and level counts of the device-side loop
         LoopState ls{};
         PLL_TRY(cudaMemcpyAsync(&ls, d_loop, sizeof(ls), cudaMemcpyDeviceToHost, s));
         PLL_TRY(cudaStreamSynchronize(s));
@@ -405,7 +434,8 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (opts) o = *opts;
     if (!out) return PLL_E_INVAL;
     *out = nullptr;
-    if (o.reserved != 0 || (o.flags & ~PLL_BUILD_HOST_LEVELS) != 0) return PLL_E_INVAL;
+    if (o.reserved != 0 || (o.flags & ~(PLL_BUILD_HOST_LEVELS | PLL_BUILD_GRAPH_LEVELS)) != 0)
+        return PLL_E_INVAL;
     if (o.t > PLL_MAX_T) return PLL_E_RANGE;
     if (n > MAX_N || nnz >= 0xffffffffull) return PLL_E_RANGE;
     if (n > 0 && !off) return PLL_E_INVAL;
@@ -529,7 +559,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     // ---- 3 + 4. pruned labels
     tm.start();
     PLL_CHECK(pruned_stage(ix, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), m_inX.as<uint8_t>(),
-                           bmax, block, (o.flags & PLL_BUILD_HOST_LEVELS) != 0, s));
+                           bmax, block, o.flags, s));
     ix->stats.ms_pruned = tm.stop_ms();
 
     PLL_TRY(dev_malloc(&ix->d_qerr, 16));

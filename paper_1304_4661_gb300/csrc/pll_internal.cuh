@@ -231,6 +231,7 @@ struct LoopState {
     unsigned long long timeout_ns;      // longest barrier wait
     unsigned long long ns_expand, ns_test;  // phase wall times (block 0)
     unsigned long long levels;          // levels run
+    unsigned long long t_mark;          // graph loop: start of the current phase
 };
 
 struct LevelDesc {
@@ -277,6 +278,10 @@ int batch_level(const BatchArgs &a, const int *grid, uint32_t block, cudaStream_
 // batch_levels_grid; 0 there means cooperative launches are unavailable)
 int batch_levels_grid(uint32_t block, int *grid);
 int batch_levels(const BatchArgs &a, uint32_t block, int grid, cudaStream_t s);
+// the level loop as a CUDA graph (a while node over the two sweeps), reading
+// the batch's arguments from d_args; one instantiation serves every batch
+int batch_graph_build(uint32_t block, const int *grid, const BatchArgs *d_args, cudaGraph_t *g,
+                      cudaGraphExec_t *exec);
 // lazy reset of the visited bitmap after a batch: clears the words of the
 // roots and of every recorded candidate (all bits the batch set)
 int batch_clear(const BatchArgs &a, int grid, cudaStream_t s);

@@ -43,6 +43,7 @@ PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 PLL_BUILD_HOST_LEVELS = 1  # pll_build_opts.flags: levels enqueued by the host
+PLL_BUILD_GRAPH_LEVELS = 2  # pll_build_opts.flags: levels as one CUDA graph launch (while node)
 
 
 class BuildOpts(C.Structure):

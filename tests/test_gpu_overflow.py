@@ -122,18 +122,19 @@ def test_finite_distance_beyond_255_is_a_range_error(t):
     (lambda: graphs.path(255), 2, 0),
 ])
 def test_host_and_device_level_loops_give_the_oracle_labels(make, t, root_batch):
-    """Both ways of running a batch's levels (PLL_BUILD_HOST_LEVELS: separate
-    launches enqueued by the host; default: one cooperative launch per batch)
-    give the oracle's labels; the default one really ran."""
+    """The three ways of running a batch's levels (default: one cooperative
+    launch per batch; PLL_BUILD_HOST_LEVELS: separate launches enqueued by the
+    host; PLL_BUILD_GRAPH_LEVELS: one CUDA graph launch whose while node runs
+    the sweeps) give the oracle's labels; the device-side ones really ran."""
     g = make()
     ref = oracle.Index(g.offsets, g.cols, t)
     Lref = ref.labels()
-    for flags in (0, pll.PLL_BUILD_HOST_LEVELS):
+    for flags in (0, pll.PLL_BUILD_HOST_LEVELS, pll.PLL_BUILD_GRAPH_LEVELS):
         ix = gpu_build(g, t, root_batch=root_batch, flags=flags)
         La = ix.labels()
         assert same_labels(La, Lref), (flags, first_label_diff(La, Lref, g.n))
         st = ix.stats()
-        if flags:
+        if flags == pll.PLL_BUILD_HOST_LEVELS:
             assert st["levels_launches"] == 0
         elif g.nnz:
             assert st["levels_launches"] == st["batches"] > 0
