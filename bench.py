@@ -47,11 +47,7 @@ WORKLOADS = {
 # launch of one build of a smaller R-MAT (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass), valid only for the kernel source with this
 # hash (else traffic is reported as null).
-PROFILED = {
-    # R-MAT-18, t = 64: 24 launches, 4.687 GB of DRAM traffic against 6.953 GB of
-    # algorithmic bytes (the oracle's sequential counts)
-    "k_batch_levels": {"src_sha": "75bfd7f24c5cbc0b", "dram_per_alg_byte": 0.674},
-}
+PROFILED = {}
 
 
 def make_graph(w):
@@ -374,11 +370,14 @@ def run_ours(args, w, ws, rank, local):
     # the result byte, and both labels (4 bytes per entry; Lsz is by vertex id)
     q_bytes = q * (8 + 8 + 2 * t + 32 + 1) + 4 * int(Lsz[s].sum() + Lsz[u].sum())
     if st["levels_launches"]:
-        # one cooperative launch per root batch runs both sweeps of every level;
-        # its phases' wall times split the time between them
+        # one launch per root batch (a CUDA graph whose while node runs both
+        # sweeps of every level, or one cooperative kernel) covers every level;
+        # its phases' wall times split the time between the sweeps
+        loop_name = ("k_batch_levels" if args.flags & 4
+                     else "level-loop graph (k_batch_expand_g + k_batch_test_g)")
         kern = {
-            "k_batch_levels": {"ms_per_step": st["ms_levels"], "launches": st["levels_launches"],
-                               "bytes": exp_bytes + test_bytes},
+            loop_name: {"ms_per_step": st["ms_levels"], "launches": st["levels_launches"],
+                        "bytes": exp_bytes + test_bytes},
             "k_query": {"ms_per_step": qk_ms, "launches": 1, "bytes": q_bytes},
         }
         phases = {"expand": {"ms_per_step": st["ms_expand"], "bytes": exp_bytes},
@@ -419,7 +418,7 @@ def run_ours(args, w, ws, rank, local):
                 "phases": {k: {"ms_per_step": round(v["ms_per_step"], 3),
                                "achieved_gbs": round(v["bytes"] / max(v["ms_per_step"], 1e-9) / 1e6, 1)}
                            for k, v in phases.items()}}
-    if dom == "k_batch_levels" and seq:
+    if st["levels_launches"] and dom != "k_query" and seq:
         gb = expand_bytes(gpu_units) + test_bytes_of(gpu_units)
         ga = gb / max(kd["ms_per_step"], 1e-9) / 1e6
         roofline["with_gpu_counts"] = {"achieved": round(ga, 1), "frac": round(ga / hbm, 4),
@@ -1154,11 +1153,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--host-levels", action="store_true",
                     help="run each root batch's levels as separate launches (PLL_BUILD_HOST_LEVELS)")
-    ap.add_argument("--graph-levels", action="store_true",
-                    help="run each root batch's levels as one CUDA graph launch (PLL_BUILD_GRAPH_LEVELS)")
+    ap.add_argument("--coop-levels", action="store_true",
+                    help="run each root batch's levels as one cooperative launch (PLL_BUILD_COOP_LEVELS)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    args.flags = (1 if args.host_levels else 0) | (2 if args.graph_levels else 0)  # PLL_BUILD_*_LEVELS
+    args.flags = (1 if args.host_levels else 0) | (4 if args.coop_levels else 0)  # PLL_BUILD_*_LEVELS
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload in ("batch256", "serve", "learned", "variants", "paths", "directed"):

@@ -66,17 +66,22 @@ typedef enum pll_status {
 typedef struct pll_index pll_index;
 
 /* Build options. Zero-initialise and set what you need. */
-/* pll_build_opts.flags: the host enqueues the levels of each root batch as
- * separate launches and reads a counter block back every few levels, instead
- * of one cooperative launch that runs every level of the batch on the device.
- * Same labels either way; also taken when the device cannot launch
- * cooperatively. */
+/* pll_build_opts.flags: how the levels of each root batch run (the same
+ * labels every way).
+ *   PLL_BUILD_GRAPH_LEVELS (the default, also with flags 0): one CUDA graph
+ *     launch per batch, a conditional while node over the expand and test
+ *     sweeps (separate kernels); a device-side step after each level stops it
+ *     when the frontier is empty. No host read-back within a batch.
+ *   PLL_BUILD_COOP_LEVELS: one cooperative launch per batch that runs every
+ *     level itself, with grid barriers whose waits are bounded (a wait that
+ *     runs out is PLL_E_TIMEOUT); falls back to the graph where the device
+ *     cannot launch cooperatively.
+ *   PLL_BUILD_HOST_LEVELS: the host enqueues the sweeps of each level as
+ *     separate launches and reads a counter block back every few levels; it
+ *     takes precedence over the other two. */
 #define PLL_BUILD_HOST_LEVELS 1u
-/* pll_build_opts.flags: the levels of each root batch run as one CUDA graph
- * launch, a conditional while node over the expand and test sweeps (separate
- * kernels) that a device-side step stops when the frontier is empty. Same
- * labels; PLL_BUILD_HOST_LEVELS takes precedence. */
 #define PLL_BUILD_GRAPH_LEVELS 2u
+#define PLL_BUILD_COOP_LEVELS 4u
 
 typedef struct pll_build_opts {
     uint32_t t;          /* bit-parallel roots, 0..PLL_MAX_T (Sec. 5.4). */
@@ -87,7 +92,7 @@ typedef struct pll_build_opts {
                             gives the same labels. */
     uint32_t block;      /* threads per CTA of the pruned-BFS kernel: 128,
                             256, 512 or 1024; 0 = library default (256). */
-    uint32_t flags;      /* 0, PLL_BUILD_HOST_LEVELS or PLL_BUILD_GRAPH_LEVELS. */
+    uint32_t flags;      /* 0 or one of PLL_BUILD_*_LEVELS (below). */
     uint64_t reserved;   /* must be 0. */
 } pll_build_opts;
 
@@ -127,9 +132,10 @@ typedef struct pll_stats {
     uint64_t pool_regrows;       /* times the label pool was moved to a larger one */
     uint64_t table_fallbacks;    /* batches whose root tables did not all fit
                                     (those roots' labels were binary-searched) */
-    /* the device-side level loop (one cooperative launch per root batch; 0
-       under PLL_BUILD_HOST_LEVELS): its launches and their CUDA-event time.
-       ms_expand / ms_test are then the wall times of its two phases. */
+    /* the device-side level loop (one graph or cooperative launch per root
+       batch; 0 under PLL_BUILD_HOST_LEVELS): its launches and their
+       CUDA-event time. ms_expand / ms_test are then the wall times of its two
+       phases. */
     uint64_t levels_launches;
     double ms_levels;
 } pll_stats;
@@ -617,9 +623,10 @@ PLL_API int64_t pll_test_live_allocs(void);
 PLL_API void pll_test_capacities(uint64_t cand, uint64_t out, uint64_t pool, uint64_t tables);
 
 /*
- * Test hook for the bounded waits of the device-side level loop; the paper has
- * no counterpart. pll_test_barrier_timeout(ns) sets the longest time a CTA
- * waits at one grid barrier of later builds (0 = the default of 10 s). A wait
+ * Test hook for the bounded waits of the cooperative level loop
+ * (PLL_BUILD_COOP_LEVELS); the paper has no counterpart.
+ * pll_test_barrier_timeout(ns) sets the longest time a CTA waits at one grid
+ * barrier of later builds (0 = the default of 10 s). A wait
  * that runs out makes the build return PLL_E_TIMEOUT, with every CTA gone from
  * the kernel and the context usable. Process-wide.
  */

@@ -93,8 +93,11 @@ struct Timer {
 // Step 3: batched pruned BFS + cleanup + append, then step 4.
 int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, const uint8_t *inX,
                  uint32_t bmax, uint32_t block, uint32_t flags, cudaStream_t s) {
+    // how each batch's levels run: a CUDA graph whose while node loops over
+    // the two sweeps (the default), one cooperative persistent launch, or
+    // separate launches enqueued by the host
     const bool host_levels = (flags & PLL_BUILD_HOST_LEVELS) != 0;
-    const bool graph_levels = !host_levels && (flags & PLL_BUILD_GRAPH_LEVELS) != 0;
+    const bool coop_levels = !host_levels && (flags & PLL_BUILD_COOP_LEVELS) != 0;
     const uint32_t n = ix->n;
     LabelStore st;
     st.n = n;
@@ -130,8 +133,9 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     // enqueues the levels itself when asked to, or when the device cannot
     // launch cooperatively)
     int lgrid = 0;
-    if (!host_levels && !graph_levels) PLL_CHECK(batch_levels_grid(block, &lgrid));
-    const bool device_levels = lgrid > 0;
+    if (coop_levels) PLL_CHECK(batch_levels_grid(block, &lgrid));
+    const bool device_levels = lgrid > 0;  // the cooperative launch is available
+    const bool graph_levels = !host_levels && !device_levels;
     DevMem m_loop;
     PLL_CHECK(m_loop.alloc(sizeof(LoopState)));
     LoopState *d_loop = m_loop.as<LoopState>();
@@ -212,8 +216,8 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         }
     } ev_guard{ev0, ev1, sweep_ev};
 
-    // the level loop as a CUDA graph (PLL_BUILD_GRAPH_LEVELS): instantiated
-    // once, launched per batch after the batch's arguments are copied in
+    // the level loop as a CUDA graph: instantiated once, launched per batch
+    // after the batch's arguments are copied in
     DevMem m_args;
     cudaGraph_t lgraph = nullptr;
     cudaGraphExec_t lexec = nullptr;
@@ -434,7 +438,8 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (opts) o = *opts;
     if (!out) return PLL_E_INVAL;
     *out = nullptr;
-    if (o.reserved != 0 || (o.flags & ~(PLL_BUILD_HOST_LEVELS | PLL_BUILD_GRAPH_LEVELS)) != 0)
+    if (o.reserved != 0 ||
+        (o.flags & ~(PLL_BUILD_HOST_LEVELS | PLL_BUILD_GRAPH_LEVELS | PLL_BUILD_COOP_LEVELS)) != 0)
         return PLL_E_INVAL;
     if (o.t > PLL_MAX_T) return PLL_E_RANGE;
     if (n > MAX_N || nnz >= 0xffffffffull) return PLL_E_RANGE;

@@ -42,8 +42,10 @@ MLP_NPARAM = 4801
 PLL_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
-PLL_BUILD_HOST_LEVELS = 1  # pll_build_opts.flags: levels enqueued by the host
-PLL_BUILD_GRAPH_LEVELS = 2  # pll_build_opts.flags: levels as one CUDA graph launch (while node)
+# pll_build_opts.flags: how each root batch's levels run
+PLL_BUILD_HOST_LEVELS = 1   # separate launches enqueued by the host
+PLL_BUILD_GRAPH_LEVELS = 2  # one CUDA graph launch with a while node (the default)
+PLL_BUILD_COOP_LEVELS = 4   # one cooperative persistent launch
 
 
 class BuildOpts(C.Structure):

@@ -122,14 +122,15 @@ def test_finite_distance_beyond_255_is_a_range_error(t):
     (lambda: graphs.path(255), 2, 0),
 ])
 def test_host_and_device_level_loops_give_the_oracle_labels(make, t, root_batch):
-    """The three ways of running a batch's levels (default: one cooperative
-    launch per batch; PLL_BUILD_HOST_LEVELS: separate launches enqueued by the
-    host; PLL_BUILD_GRAPH_LEVELS: one CUDA graph launch whose while node runs
-    the sweeps) give the oracle's labels; the device-side ones really ran."""
+    """The three ways of running a batch's levels (default: one CUDA graph
+    launch per batch whose while node runs the sweeps; PLL_BUILD_HOST_LEVELS:
+    separate launches enqueued by the host; PLL_BUILD_COOP_LEVELS: one
+    cooperative launch per batch) give the oracle's labels; the device-side
+    ones really ran."""
     g = make()
     ref = oracle.Index(g.offsets, g.cols, t)
     Lref = ref.labels()
-    for flags in (0, pll.PLL_BUILD_HOST_LEVELS, pll.PLL_BUILD_GRAPH_LEVELS):
+    for flags in (0, pll.PLL_BUILD_HOST_LEVELS, pll.PLL_BUILD_COOP_LEVELS):
         ix = gpu_build(g, t, root_batch=root_batch, flags=flags)
         La = ix.labels()
         assert same_labels(La, Lref), (flags, first_label_diff(La, Lref, g.n))
@@ -141,8 +142,8 @@ def test_host_and_device_level_loops_give_the_oracle_labels(make, t, root_batch)
 
 
 def test_barrier_wait_that_runs_out_returns_timeout_and_the_gpu_stays_usable():
-    """A grid barrier of the level loop that waits past its limit makes the
-    build return PLL_E_TIMEOUT: the limit is set to 1 ns, so every CTA but the
+    """A grid barrier of the cooperative level loop that waits past its limit
+    makes the build return PLL_E_TIMEOUT: the limit is set to 1 ns, so every CTA but the
     last to arrive gives up at the first barrier and leaves the kernel. No
     allocation leaks, and the next build (default limit) is exact."""
     import gc
@@ -155,12 +156,12 @@ def test_barrier_wait_that_runs_out_returns_timeout_and_the_gpu_stays_usable():
         lib.pll_test_barrier_timeout(1)
         try:
             with pytest.raises(pll.PLLError) as e:
-                gpu_build(g, 16)
+                gpu_build(g, 16, flags=pll.PLL_BUILD_COOP_LEVELS)
             assert e.value.code == pll.PLL_E_TIMEOUT
         finally:
             lib.pll_test_barrier_timeout(0)
         assert lib.pll_test_live_allocs() == live
     finally:
         gc.enable()
-    ix = gpu_build(g, 16)
+    ix = gpu_build(g, 16, flags=pll.PLL_BUILD_COOP_LEVELS)
     assert same_labels(ix.labels(), oracle.Index(g.offsets, g.cols, 16).labels())
