@@ -679,7 +679,19 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
             const uint32_t j = __ffs(m) - 1;
             const uint32_t lj = __shfl_sync(FULL, wlen, j);
             const unsigned long long base = tc[j].lab_base + __shfl_sync(FULL, excl, j);
-            for (uint32_t x0 = 0; x0 < lj; x0 += 32 * U) {
+            // the first 32 entries alone (most candidates that a label prunes
+            // are pruned by their first hubs, the highest-ranked), then U
+            // rounds per step
+            {
+                uint32_t e1[1], o1[1] = {j};
+                bool a1[1] = {true};
+                e1[0] = a.pool[base + lane];
+                if (__any_sync(FULL, lookup_entries(a, tc, e1, o1, a1, level, n_scan) != 0)) {
+                    pruned |= 1u << j;
+                    continue;
+                }
+            }
+            for (uint32_t x0 = 32; x0 < lj; x0 += 32 * U) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const uint32_t x = x0 + 32 * u + lane;
