@@ -679,10 +679,12 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
             const uint32_t j = __ffs(m) - 1;
             const uint32_t lj = __shfl_sync(FULL, wlen, j);
             const unsigned long long base = tc[j].lab_base + __shfl_sync(FULL, excl, j);
-            // the first 32 entries alone (most candidates that a label prunes
-            // are pruned by their first hubs, the highest-ranked), then U
-            // rounds per step
-            {
+            // without bit-parallel labels (t = 0) the labels prune most
+            // candidates, mostly with their first hubs (the highest-ranked):
+            // the first 32 entries alone, then U rounds per step. With them,
+            // most candidates that reach this test survive it and need every
+            // entry, so U rounds from the start.
+            if (a.t == 0) {
                 uint32_t e1[1], o1[1] = {j};
                 bool a1[1] = {true};
                 e1[0] = a.pool[base + lane];
@@ -691,7 +693,7 @@ __device__ __forceinline__ void test_body(const BatchArgs &a, unsigned long long
                     continue;
                 }
             }
-            for (uint32_t x0 = 32; x0 < lj; x0 += 32 * U) {
+            for (uint32_t x0 = a.t == 0 ? 32u : 0u; x0 < lj; x0 += 32 * U) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const uint32_t x = x0 + 32 * u + lane;
