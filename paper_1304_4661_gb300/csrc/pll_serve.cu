@@ -43,6 +43,23 @@
 #include "pll_internal.cuh"
 #include "serve_ring.h"
 
+// Locking. Every request passes through three hands (its client, the
+// dispatcher, its waiter), so no lock is held across a sleep and none is
+// shared by all of them:
+//   * the ring (admission, the FIFO of live requests, the stream slots'
+//     bookkeeping, the statistics) is guarded by a spin lock held for a few
+//     dozen instructions: a contended hand-off is a cache-line transfer, not a
+//     futex sleep and wake-up, which would cap the whole server at one
+//     request per wake-up latency;
+//   * tickets live in 64 shards, each with its own mutex;
+//   * completion is a per-request flag; a waiter spins on it for a while and
+//     only then sleeps on its shard's condition variable, which the
+//     dispatcher signals only when someone sleeps there.
+// Sleeping on a condition variable (a full ring, an idle dispatcher, a
+// waiter) always re-checks its condition under the mutex after announcing
+// itself in a counter, and the other side reads that counter after making
+// the condition true (both sequentially consistent), so no wake-up is lost.
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -53,9 +70,10 @@ struct Request {
     uint8_t *out = nullptr;
     Clock::time_point t_submit;
     double latency_us = 0;
-    std::atomic<bool> staged{false};  // set by the client once its pairs are in place
-    bool done = false;
     int status = PLL_OK;
+    bool waiting = false;               // a pll_server_wait holds it (shard lock)
+    std::atomic<bool> staged{false};    // set by the client once its pairs are in place
+    std::atomic<bool> done{false};      // set by the dispatcher once its results are delivered
 };
 
 struct Run {
@@ -68,11 +86,42 @@ struct Run {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t start = nullptr, done = nullptr;
-    bool busy = false;
+    bool busy = false;  // dispatcher thread only
 };
+
+class SpinLock {
+    std::atomic<bool> held_{false};
+
+  public:
+    void lock() {
+        for (unsigned spins = 0;;) {
+            if (!held_.exchange(true, std::memory_order_acquire)) return;
+            while (held_.load(std::memory_order_relaxed))
+                if (++spins > 256) std::this_thread::yield();
+        }
+    }
+    void unlock() { held_.store(false, std::memory_order_release); }
+};
+
+struct alignas(64) Shard {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::unordered_map<uint64_t, Request *> map;
+    std::atomic<int> sleepers{0};
+};
+
+constexpr int SHARDS = 64;
 
 double us_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+// Wake whoever sleeps on (mu, cv) after `count` announced itself; the caller
+// has already made the awaited condition true.
+void wake(std::mutex &mu, std::condition_variable &cv, const std::atomic<int> &count) {
+    if (count.load(std::memory_order_seq_cst) == 0) return;
+    { std::lock_guard<std::mutex> lock(mu); }
+    cv.notify_all();
 }
 
 }  // namespace
@@ -90,20 +139,25 @@ struct pll_server {
     std::vector<Slot> slots;
     std::deque<Run> inflight;         // dispatcher thread only, launch order
     double device_us = 0;             // dispatcher thread only
-    std::mutex mu;                    // guards everything below
-    std::condition_variable cv_work;  // dispatcher: a request was staged, or stop
-    std::condition_variable cv_done;  // clients: a request completed
-    std::condition_variable cv_space; // clients: ring slots were freed
+    // ---- guarded by `ring`
+    SpinLock ring;
     std::deque<Request *> live;       // hold ring slots, ring order
     size_t nlaunched = 0;             // live[0, nlaunched) belong to launched runs
-    std::unordered_map<uint64_t, Request *> table;
     uint64_t next_ticket = 1;
-    bool stop = false;
-    std::thread worker;
     pll_server_stats st{};
+    // ---- tickets
+    Shard shards[SHARDS];
+    // ---- sleeping: a full ring (clients), an idle dispatcher
+    std::mutex space_mu, work_mu;
+    std::condition_variable cv_space, cv_work;
+    std::atomic<int> space_sleepers{0}, work_sleepers{0};
+    std::atomic<bool> stop{false};
+    std::thread worker;
     std::atomic<unsigned long long> pack_ns{0};  // client staging time (no lock)
     std::atomic<uint64_t> staged_seq{0};         // bumped by every staged request
     int fatal = PLL_OK;
+
+    Shard &shard(uint64_t ticket) { return shards[ticket % SHARDS]; }
 };
 
 namespace {
@@ -131,29 +185,31 @@ int launch_run(pll_server *sv, const Run &r) {
     return PLL_OK;
 }
 
-// Deliver a run's results and return its slots to the ring.
+// Deliver a run's results, return its slots to the ring, then mark its
+// requests done (a waiter may free a request the moment it sees the flag, so
+// the ring lets go of them first).
 void retire_run(pll_server *sv, const Run &r, int status) {
     const Clock::time_point t0 = Clock::now();
     if (status == PLL_OK)
         for (const Request *q : r.reqs)  // the caller's buffer is ours until done is set
             if (q->ticket) std::memcpy(q->out, sv->h_out + q->off, q->q);
     const Clock::time_point now = Clock::now();
-    {
-        std::lock_guard<std::mutex> lock(sv->mu);
-        for (Request *q : r.reqs) {
-            if (q->ticket == 0) { delete q; continue; }
-            q->latency_us = us_between(q->t_submit, now);
-            q->status = status;
-            q->done = true;
-        }
-        for (size_t i = 0; i < r.reqs.size(); ++i) sv->live.pop_front();
-        sv->nlaunched -= r.reqs.size();
-        sv->slots[r.slot].busy = false;
-        sv->st.unpack_us += us_between(t0, now);
-        sv->st.device_us = sv->device_us;
+    sv->slots[r.slot].busy = false;
+    sv->ring.lock();
+    for (size_t i = 0; i < r.reqs.size(); ++i) sv->live.pop_front();
+    sv->nlaunched -= r.reqs.size();
+    sv->st.unpack_us += us_between(t0, now);
+    sv->st.device_us = sv->device_us;
+    sv->ring.unlock();
+    wake(sv->space_mu, sv->cv_space, sv->space_sleepers);
+    for (Request *q : r.reqs) {
+        if (q->ticket == 0) { delete q; continue; }
+        Shard &sh = sv->shard(q->ticket);
+        q->latency_us = us_between(q->t_submit, now);
+        q->status = status;
+        q->done.store(true, std::memory_order_seq_cst);  // q may be gone after this
+        wake(sh.mu, sh.cv, sh.sleepers);
     }
-    sv->cv_done.notify_all();
-    sv->cv_space.notify_all();
 }
 
 void worker_loop(pll_server *sv) {
@@ -162,7 +218,7 @@ void worker_loop(pll_server *sv) {
     // condition variable: a thread woken from sleep adds tens of microseconds
     constexpr int SPIN_US = 1000;
     Clock::time_point last_work = Clock::now();
-    uint64_t seen_seq = ~0ull;  // staged_seq at the last look under the lock
+    uint64_t seen_seq = ~0ull;  // staged_seq at the last look at the ring
     bool leftover = false;
     for (;;) {
         // 1. retire finished runs, oldest first
@@ -184,32 +240,27 @@ void worker_loop(pll_server *sv) {
             sv->inflight.pop_front();
             last_work = Clock::now();
         }
-        // 2. with a free stream slot, launch the staged requests as one run
+        // 2. with a free stream slot, launch the staged requests as one run;
+        // the ring is looked at only when a run could be launched (a slot is
+        // free and requests were staged since the last look, or some were left
+        // over) or when nothing is in flight (to sleep or to stop)
         int slot = -1;
         for (size_t i = 0; i < sv->slots.size(); ++i)
             if (!sv->slots[i].busy) { slot = (int)i; break; }
         Run run;
-        bool quit = false;
-        // the lock is taken only when a run could be launched (a slot is free
-        // and requests were staged since the last look, or some were left
-        // over) or when nothing is in flight (to sleep or to stop); otherwise
-        // the loop just polls the runs in flight, leaving the lock to clients
-        const uint64_t seq = sv->staged_seq.load(std::memory_order_acquire);
-        const bool look = sv->inflight.empty() || (slot >= 0 && (seq != seen_seq || leftover));
-        if (look) {
+        const uint64_t seq = sv->staged_seq.load(std::memory_order_seq_cst);
+        const bool idle = sv->inflight.empty();
+        if (idle || (slot >= 0 && (seq != seen_seq || leftover))) {
             seen_seq = seq;
-            std::unique_lock<std::mutex> lock(sv->mu);
-            auto ready = [sv] {
+            bool empty = false, ready = false;
+            sv->ring.lock();
+            auto first_staged = [sv] {
                 return sv->nlaunched < sv->live.size() &&
                        sv->live[sv->nlaunched]->staged.load(std::memory_order_acquire);
             };
-            if (!ready() && sv->inflight.empty()) {
-                if (sv->stop && sv->live.empty()) quit = true;
-                else if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US))
-                    sv->cv_work.wait_for(lock, std::chrono::milliseconds(2),
-                                         [&] { return sv->stop || ready(); });
-            }
-            if (!quit && slot >= 0 && ready()) {
+            ready = first_staged();
+            empty = sv->live.empty();
+            if (slot >= 0 && ready) {
                 run.off = sv->live[sv->nlaunched]->off;
                 for (size_t i = sv->nlaunched; i < sv->live.size(); ++i) {
                     Request *q = sv->live[i];
@@ -221,14 +272,27 @@ void worker_loop(pll_server *sv) {
                 }
                 sv->nlaunched += run.reqs.size();
                 run.slot = slot;
-                sv->slots[slot].busy = true;
                 sv->st.batches++;
                 sv->st.max_batch_pairs = std::max(sv->st.max_batch_pairs, run.pairs);
             }
-            leftover = ready();  // staged requests the run did not take (size, wrap)
+            leftover = first_staged();  // staged requests the run did not take (size, wrap)
+            sv->ring.unlock();
+            if (idle && !ready) {
+                if (sv->stop.load(std::memory_order_seq_cst) && empty) return;
+                if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US)) {
+                    std::unique_lock<std::mutex> lock(sv->work_mu);
+                    sv->work_sleepers.fetch_add(1, std::memory_order_seq_cst);
+                    sv->cv_work.wait_for(lock, std::chrono::milliseconds(2), [&] {
+                        return sv->stop.load(std::memory_order_seq_cst) ||
+                               sv->staged_seq.load(std::memory_order_seq_cst) != seq;
+                    });
+                    sv->work_sleepers.fetch_sub(1, std::memory_order_seq_cst);
+                }
+                continue;
+            }
         }
-        if (quit) return;
         if (run.slot >= 0) {
+            sv->slots[run.slot].busy = true;
             const int s = launch_run(sv, run);
             if (s != PLL_OK) {
                 // nothing of the run is in flight once the stream drains; it
@@ -253,10 +317,11 @@ void destroy(pll_server *sv) {
         if (sl.done) cudaEventDestroy(sl.done);
     }
     if (sv->h_pairs) cudaFreeHost(sv->h_pairs);
-    // a request is in `live` until it completes, and in `table` from staging
-    // until it is waited for: completed ones are only in the table
-    for (auto &kv : sv->table)
-        if (kv.second->done) delete kv.second;
+    // a request is in `live` until its run retires, and in its shard from
+    // staging until it is waited for: completed ones are only in a shard
+    for (Shard &sh : sv->shards)
+        for (auto &kv : sh.map)
+            if (kv.second->done.load()) delete kv.second;
     for (Request *r : sv->live) delete r;
     delete sv;
 }
@@ -324,18 +389,37 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
     r->q = q;
     r->out = out;
     r->t_submit = Clock::now();
+    // admission: q contiguous ring slots, else sleep until a run retires
+    for (bool admitted = false; !admitted;) {
+        if (sv->stop.load(std::memory_order_seq_cst)) { delete r; return PLL_E_INVAL; }
+        auto try_admit = [&] {
+            uint64_t off = 0;
+            sv->ring.lock();
+            const bool ok = ring_alloc(sv->live, sv->P, q, &off);
+            if (ok) {
+                r->off = off;
+                r->ticket = sv->next_ticket++;
+                sv->live.push_back(r);
+                sv->st.max_inflight_bytes = std::max(sv->st.max_inflight_bytes, 9 * ring_used(sv->live, sv->P));
+                sv->st.requests++;
+                sv->st.pairs += q;
+            }
+            sv->ring.unlock();
+            return ok;
+        };
+        if (try_admit()) break;
+        std::unique_lock<std::mutex> lock(sv->space_mu);
+        sv->space_sleepers.fetch_add(1, std::memory_order_seq_cst);
+        admitted = try_admit();
+        if (!admitted)
+            sv->cv_space.wait_for(lock, std::chrono::milliseconds(10));
+        sv->space_sleepers.fetch_sub(1, std::memory_order_seq_cst);
+    }
+    const uint64_t tk = r->ticket;
+    Shard &sh = sv->shard(tk);
     {
-        std::unique_lock<std::mutex> lock(sv->mu);
-        uint64_t off = 0;
-        sv->cv_space.wait(lock, [&] { return sv->stop || ring_alloc(sv->live, sv->P, q, &off); });
-        if (sv->stop) { delete r; return PLL_E_INVAL; }
-        r->off = off;
-        r->ticket = sv->next_ticket++;
-        sv->table[r->ticket] = r;
-        sv->live.push_back(r);
-        sv->st.max_inflight_bytes = std::max(sv->st.max_inflight_bytes, 9 * ring_used(sv->live, sv->P));
-        sv->st.requests++;
-        sv->st.pairs += q;
+        std::lock_guard<std::mutex> lock(sh.mu);
+        sh.map[tk] = r;
     }
     // stage the pairs into the request's own slots, checking the ids on the way
     const Clock::time_point t0 = Clock::now();
@@ -348,16 +432,15 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
         h[2 * i] = a < n ? a : 0;
         h[2 * i + 1] = b < n ? b : 0;
     }
-    const uint64_t tk = r->ticket;
     if (bad) {  // keeps its slots until its run retires, answers nobody
-        std::lock_guard<std::mutex> lock(sv->mu);
-        sv->table.erase(tk);
+        std::lock_guard<std::mutex> lock(sh.mu);
+        sh.map.erase(tk);
         r->ticket = 0;
     }
     sv->pack_ns.fetch_add((unsigned long long)(us_between(t0, Clock::now()) * 1e3), std::memory_order_relaxed);
     r->staged.store(true, std::memory_order_release);  // pairs and ticket before the flag
-    sv->staged_seq.fetch_add(1, std::memory_order_release);
-    sv->cv_work.notify_one();
+    sv->staged_seq.fetch_add(1, std::memory_order_seq_cst);
+    wake(sv->work_mu, sv->cv_work, sv->work_sleepers);
     if (bad) return PLL_E_INVAL;
     *ticket = tk;
     return PLL_OK;
@@ -365,17 +448,51 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
 
 PLL_API int pll_server_wait(pll_server *sv, uint64_t ticket, int64_t timeout_us, double *latency_us) {
     if (!sv) return PLL_E_INVAL;
-    std::unique_lock<std::mutex> lock(sv->mu);
-    auto it = sv->table.find(ticket);
-    if (it == sv->table.end()) return PLL_E_INVAL;
-    Request *r = it->second;
-    auto ready = [r] { return r->done; };
-    if (timeout_us < 0) sv->cv_done.wait(lock, ready);
-    else if (!sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), ready))
-        return PLL_E_TIMEOUT;
+    Shard &sh = sv->shard(ticket);
+    Request *r = nullptr;
+    bool finished = false;
+    {
+        std::lock_guard<std::mutex> lock(sh.mu);
+        auto it = sh.map.find(ticket);
+        if (it == sh.map.end() || it->second->waiting) return PLL_E_INVAL;
+        r = it->second;
+        finished = r->done.load(std::memory_order_seq_cst);
+        if (finished) sh.map.erase(it);  // done already: released in the same visit
+        else r->waiting = true;          // no other wait may release it meanwhile
+    }
+    auto done = [r] { return r->done.load(std::memory_order_seq_cst); };
+    if (finished) {
+        if (latency_us) *latency_us = r->latency_us;
+        const int s = r->status;
+        delete r;
+        return s;
+    }
+    {
+        // poll for up to SPIN_US (a run is usually tens of microseconds from
+        // retiring), then sleep until the dispatcher signals the shard
+        constexpr int64_t SPIN_US = 50;
+        const Clock::time_point t0 = Clock::now();
+        const int64_t spin = timeout_us < 0 ? SPIN_US : std::min<int64_t>(SPIN_US, timeout_us);
+        while (!done() && Clock::now() - t0 < std::chrono::microseconds(spin)) std::this_thread::yield();
+        if (!done()) {
+            std::unique_lock<std::mutex> lock(sh.mu);
+            sh.sleepers.fetch_add(1, std::memory_order_seq_cst);
+            bool ok = true;
+            if (timeout_us < 0) sh.cv.wait(lock, done);
+            else ok = sh.cv.wait_until(lock, t0 + std::chrono::microseconds(timeout_us), done);
+            sh.sleepers.fetch_sub(1, std::memory_order_seq_cst);
+            if (!ok) {
+                r->waiting = false;
+                return PLL_E_TIMEOUT;
+            }
+        }
+    }
     if (latency_us) *latency_us = r->latency_us;
     const int s = r->status;
-    sv->table.erase(it);
+    {
+        std::lock_guard<std::mutex> lock(sh.mu);
+        sh.map.erase(ticket);
+    }
     delete r;
     return s;
 }
@@ -392,7 +509,7 @@ PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_
             return PLL_E_INVAL;
     if (threads == 0) threads = 1;
     // client thread k submits requests k, k + threads, ... at their arrival
-    // times; one collector waits for them in order
+    // times; collector c of C waits for requests c, c + C, ... in order
     std::vector<uint64_t> tickets(count, 0);
     std::unique_ptr<std::atomic<uint8_t>[]> posted(new (std::nothrow) std::atomic<uint8_t>[count ? count : 1]);
     if (!posted) return PLL_E_NOMEM;
@@ -418,19 +535,29 @@ PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_
             posted[i].store(1, std::memory_order_release);
         }
     };
+    // one collector per four clients: releasing a ticket costs about as much
+    // host time as submitting a small request
+    const uint32_t C = std::max<uint32_t>(1, threads / 4);
+    auto collector = [&](uint32_t c) {
+        for (uint64_t i = c; i < count; i += C) {
+            while (!posted[i].load(std::memory_order_acquire)) std::this_thread::yield();
+            if (tickets[i] != 0) note(pll_server_wait(sv, tickets[i], -1, &latency_us[i]));
+        }
+    };
     std::vector<std::thread> pool;
+    uint32_t started = 1, collectors = 0;  // client 0 runs on this thread
     try {
-        for (uint32_t k = 1; k < threads; ++k) pool.emplace_back(client, k);
-        pool.emplace_back([&] {
-            for (uint64_t i = 0; i < count; ++i) {
-                while (!posted[i].load(std::memory_order_acquire)) std::this_thread::yield();
-                if (tickets[i] != 0) note(pll_server_wait(sv, tickets[i], -1, &latency_us[i]));
-            }
-        });
-    } catch (...) {  // the collector starts last: without it nothing waits on `posted`
+        for (; started < threads; ++started) pool.emplace_back(client, started);
+        for (; collectors < C; ++collectors) pool.emplace_back(collector, collectors);
+    } catch (...) {
         note(PLL_E_NOMEM);
     }
+    // clients or collectors that could not be started run here, after client
+    // 0 (with the error noted, those clients only mark their requests posted),
+    // so nothing is left waiting on `posted`
     client(0);
+    for (uint32_t k = started; k < threads; ++k) client(k);
+    for (uint32_t c = collectors; c < C; ++c) collector(c);
     for (std::thread &th : pool) th.join();
     if (elapsed_us) *elapsed_us = us_between(t0, Clock::now());
     return first_err.load();
@@ -438,19 +565,19 @@ PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_
 
 PLL_API int pll_server_get_stats(pll_server *sv, pll_server_stats *out) {
     if (!sv || !out) return PLL_E_INVAL;
-    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->ring.lock();
     *out = sv->st;
+    sv->ring.unlock();
     out->pack_us = sv->pack_ns.load(std::memory_order_relaxed) / 1e3;
     return PLL_OK;
 }
 
 PLL_API int pll_server_stop(pll_server *sv) {
     if (!sv) return PLL_OK;
-    {
-        std::lock_guard<std::mutex> lock(sv->mu);
-        sv->stop = true;
-    }
+    sv->stop.store(true, std::memory_order_seq_cst);
+    { std::lock_guard<std::mutex> lock(sv->work_mu); }
     sv->cv_work.notify_all();
+    { std::lock_guard<std::mutex> lock(sv->space_mu); }
     sv->cv_space.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     const int s = sv->fatal;
