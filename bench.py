@@ -446,8 +446,13 @@ def run_ours(args, w, ws, rank, local):
                       "pruned": round(st["ms_pruned"], 3), "pruned_bfs": round(st["ms_pruned_kernel"], 3),
                       "expand_sweeps": round(st["ms_expand"], 3), "test_sweeps": round(st["ms_test"], 3),
                       "level_loop": round(st["ms_levels"], 3),
+                      "post": round(st["ms_post"], 3),
+                      "host_gaps": round(st["ms_pruned"] - st["ms_pruned_kernel"] - st["ms_post"]
+                                         - st["ms_finalize"], 3),
                       "finalize": round(st["ms_finalize"], 3)},
         "batches": st["batches"], "pre_cleanup": st["pre_cleanup"], "visited": st["visited"],
+        "memory_gb": {"index": round(st["index_bytes"] / 1e9, 3),
+                      "build_scratch_peak": round(st["scratch_peak_bytes"] / 1e9, 3)},
         "prune_work": {"label_entries_scanned": st["pruned_scanned"], "mask_pairs": st["pruned_masks"],
                        "arcs_expanded": st["pruned_expanded"], "candidates": st["candidates"]},
         "wall_s_timed_region": round(wall, 3),

@@ -138,6 +138,13 @@ typedef struct pll_stats {
        phases. */
     uint64_t levels_launches;
     double ms_levels;
+    /* CUDA-event time of each root batch's sort, cleanup, compaction and
+       append, summed (ms_pruned less ms_pruned_kernel, ms_post and
+       ms_finalize is the time the GPU waited on the host between batches) */
+    double ms_post;
+    /* most scratch memory the build held at once (its temporaries, from the
+       library's scratch pool; the index's own arrays are index_bytes) */
+    uint64_t scratch_peak_bytes;
 } pll_stats;
 
 /*
@@ -229,7 +236,13 @@ PLL_API int pll_query_async(const pll_index *idx, const uint32_t *src, const uin
 PLL_API int pll_query_errors(const pll_index *idx, void *stream, uint64_t *count);
 
 /* pll_query_host -- as pll_query with HOST src, dst and out; the copies to
- * and from the device happen inside the call. */
+ * and from the device happen inside the call.
+ *
+ * Staging (pll_build_host, pll_query_host): the device copies live in a
+ * stream-ordered memory pool of this library, one per CUDA context, which
+ * keeps up to 1 GiB of freed staging memory mapped between calls (remapping
+ * ~100 MB on every call cost milliseconds). A staging allocation that fails
+ * returns PLL_E_NOMEM. */
 PLL_API int pll_query_host(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
                            uint64_t q, uint8_t *out, void *stream);
 
@@ -631,6 +644,18 @@ PLL_API void pll_test_capacities(uint64_t cand, uint64_t out, uint64_t pool, uin
  * the kernel and the context usable. Process-wide.
  */
 PLL_API void pll_test_barrier_timeout(uint64_t ns);
+
+/*
+ * Scratch memory. Every temporary of a build (pll_build, pll_build_host,
+ * pll_build_batch, pll_autotune's trials) and the staging copies of the
+ * host-pointer entry points are stream-ordered allocations from one memory
+ * pool of this library per CUDA context, which keeps freed scratch (up to an
+ * eighth of the device's memory) mapped so that the next call does not map
+ * and unmap pages again (about 3 ms per GiB). pll_release_cached synchronises the current device
+ * and hands the current context's cached scratch back to the driver; later
+ * calls work as before. PLL_E_CUDA if the device reports an error.
+ */
+PLL_API int pll_release_cached(void);
 
 /* Static, human-readable text for a status code. */
 PLL_API const char *pll_status_str(int status);

@@ -215,7 +215,7 @@ int bp_run(uint32_t n, uint32_t t, uint32_t graphs, const uint32_t *d_roff, cons
     PLL_TRY(cudaGetLastError());
 
     // work items: (vertex, chunk of <= CHUNK arcs)
-    DevMem cnt, coff, items, temp, flag;
+    PoolMem cnt(s), coff(s), items(s), temp(s), flag(s);
     PLL_CHECK(cnt.alloc(((size_t)n + 1) * 4));
     PLL_CHECK(coff.alloc(((size_t)n + 1) * 4));
     PLL_TRY(cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * 4, s));

@@ -164,9 +164,9 @@ inline int grid_for(uint64_t items, int block) {
 
 }  // namespace
 
-int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int end_bit, void *d_temp,
-                       size_t *temp_bytes, cudaStream_t s) {
-    PLL_TRY(cub::DeviceRadixSort::SortKeys(d_temp, *temp_bytes, d_in, d_out, (int64_t)count, 0,
+int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int begin_bit, int end_bit,
+                       void *d_temp, size_t *temp_bytes, cudaStream_t s) {
+    PLL_TRY(cub::DeviceRadixSort::SortKeys(d_temp, *temp_bytes, d_in, d_out, (int64_t)count, begin_bit,
                                            end_bit, s));
     return PLL_OK;
 }
@@ -221,16 +221,23 @@ int scan_u32_to_u64(const uint32_t *d_in, uint64_t *d_out, uint32_t n, void *d_t
 // bump pointer would run past the pool.
 int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s) {
     const uint32_t n = st.n;
-    DevMem pool, noff, temp;
-    PLL_CHECK(pool.alloc(new_cap * 4));
+    DevMem dpool;
+    PoolMem ppool(s), noff(s), temp(s);
+    uint32_t *np = nullptr;
+    if (st.pooled) {
+        PLL_CHECK(ppool.alloc(new_cap * 4));
+        np = ppool.as<uint32_t>();
+    } else {
+        PLL_CHECK(dpool.alloc(new_cap * 4));
+        np = dpool.as<uint32_t>();
+    }
     PLL_CHECK(noff.alloc(((size_t)n + 1) * 8));
     size_t tb = 0;
     PLL_CHECK(scan_u32_to_u64(st.len, noff.as<uint64_t>(), n, nullptr, &tb, s, 4));
     PLL_CHECK(temp.alloc(tb));
     PLL_CHECK(scan_u32_to_u64(st.len, noff.as<uint64_t>(), n, temp.p, &tb, s, 4));
     k_gather_labels<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(n, st.off, st.len, st.pool,
-                                                                    noff.as<uint64_t>(),
-                                                                    pool.as<uint32_t>());
+                                                                    noff.as<uint64_t>(), np);
     PLL_TRY(cudaGetLastError());
     PLL_TRY(cudaMemcpyAsync(st.off, noff.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
     k_round_caps<<<grid_for(n, 256), 256, 0, s>>>(st.len, st.cap, n);
@@ -246,9 +253,11 @@ int labels_regrow(LabelStore &st, uint64_t new_cap, cudaStream_t s) {
     unsigned long long top = last_off + ((last_len + 3u) & ~3u);
     PLL_TRY(cudaMemcpyAsync(st.pool_top, &top, 8, cudaMemcpyHostToDevice, s));
     PLL_TRY(cudaStreamSynchronize(s));
-    dev_free(st.pool);
-    st.pool = pool.as<uint32_t>();
-    pool.release();
+    if (st.pooled) pool_free(st.pool, s);
+    else dev_free(st.pool);
+    st.pool = np;
+    ppool.release();
+    dpool.release();
     st.pool_cap = new_cap;
     return PLL_OK;
 }

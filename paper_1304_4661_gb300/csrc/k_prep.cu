@@ -283,7 +283,7 @@ int prep_validate_csr(const Graph &g, uint32_t *d_err, cudaStream_t s) {
 
 int prep_degree_order(const Graph &g, uint32_t *d_order, cudaStream_t s) {
     if (g.n == 0) return PLL_OK;
-    DevMem keys, sorted, temp;
+    PoolMem keys(s), sorted(s), temp(s);
     PLL_CHECK(keys.alloc((size_t)g.n * 8));
     PLL_CHECK(sorted.alloc((size_t)g.n * 8));
     k_degree_keys<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.off, keys.as<uint64_t>());
@@ -302,7 +302,7 @@ int prep_degree_order(const Graph &g, uint32_t *d_order, cudaStream_t s) {
 
 int prep_check_order(const Graph &g, const uint32_t *d_order, uint32_t *d_err, cudaStream_t s) {
     if (g.n == 0) return PLL_OK;
-    DevMem cnt;
+    PoolMem cnt(s);
     PLL_CHECK(cnt.alloc((size_t)g.n * 4));
     PLL_TRY(cudaMemsetAsync(cnt.p, 0, (size_t)g.n * 4, s));
     k_count_order<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, d_order, cnt.as<uint32_t>(), d_err);
@@ -318,7 +318,7 @@ int prep_relabel(const Graph &g, const uint32_t *d_order, uint32_t *d_inv, uint3
         PLL_TRY(cudaMemsetAsync(d_roff, 0, 4, s));
         return PLL_OK;
     }
-    DevMem rdeg, tmpcol, temp;
+    PoolMem rdeg(s), tmpcol(s), temp(s);
     PLL_CHECK(rdeg.alloc((size_t)g.n * 4));
     k_inverse_and_degree<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, d_order, g.off, d_inv,
                                                             rdeg.as<uint32_t>());
@@ -380,7 +380,7 @@ int prep_batch_order(const Graph &g, const uint32_t *d_gs, uint32_t G, uint32_t 
     if (g.n == 0) return PLL_OK;
     k_graph_of<<<(int)std::min<uint32_t>(G, 65535), 256, 0, s>>>(G, d_gs, d_gof);
     k_check_graph_arcs<<<grid_for((uint64_t)g.n * 32, 256), 256, 0, s>>>(g.n, g.off, g.col, d_gof, d_err);
-    DevMem k1, k1s, v1, k2, temp;
+    PoolMem k1(s), k1s(s), v1(s), k2(s), temp(s);
     PLL_CHECK(k1.alloc((size_t)g.n * 8));
     PLL_CHECK(k1s.alloc((size_t)g.n * 8));
     PLL_CHECK(v1.alloc((size_t)g.n * 4));

@@ -13,9 +13,12 @@
 //   4. compaction of the labels into one hub-sorted CSR for queries.
 // Level boundaries stay on the device; the host reads a small counter block
 // every few levels (to see an empty frontier) and once after the append.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -101,7 +104,8 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     const uint32_t n = ix->n;
     LabelStore st;
     st.n = n;
-    DevMem m_off, m_len, m_cap, m_pool, m_ctr, m_desc;
+    // every temporary of the stage is stream-ordered scratch from the pool
+    PoolMem m_off(s), m_len(s), m_cap(s), m_pool(s), m_ctr(s), m_desc(s);
     PLL_CHECK(m_off.alloc((size_t)n * 8));
     PLL_CHECK(m_len.alloc((size_t)n * 4));
     PLL_CHECK(m_cap.alloc((size_t)n * 4));
@@ -120,12 +124,14 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     st.pool_cap = test_caps().pool ? test_caps().pool : std::max<uint64_t>((uint64_t)n * 16, 1ull << 22);
     PLL_CHECK(m_pool.alloc(st.pool_cap * 4));
     st.pool = m_pool.as<uint32_t>();
+    st.pooled = true;
     m_pool.release();  // owned through st.pool from here on (regrow swaps it)
     st.pool_top = &d_ctr->pool_top;
     struct PoolGuard {
         LabelStore *st;
-        ~PoolGuard() { dev_free(st->pool); }
-    } pool_guard{&st};
+        cudaStream_t s;
+        ~PoolGuard() { pool_free(st->pool, s); }
+    } pool_guard{&st, s};
 
     int grid[2] = {0, 0};
     PLL_CHECK(batch_grid(block, grid));
@@ -136,7 +142,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     if (coop_levels) PLL_CHECK(batch_levels_grid(block, &lgrid));
     const bool device_levels = lgrid > 0;  // the cooperative launch is available
     const bool graph_levels = !host_levels && !device_levels;
-    DevMem m_loop;
+    PoolMem m_loop(s);
     PLL_CHECK(m_loop.alloc(sizeof(LoopState)));
     LoopState *d_loop = m_loop.as<LoopState>();
     {
@@ -145,14 +151,15 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         PLL_TRY(cudaMemcpyAsync(d_loop, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     }
     // clamped copy of the bit-parallel distance rows for the expand sweep
-    DevMem m_bpc;
+    PoolMem m_bpc(s);
     PLL_CHECK(m_bpc.alloc(std::max<size_t>((size_t)n * ix->tp, 16)));
     PLL_CHECK(batch_clamp_rows(ix->d_bp_d, m_bpc.as<uint8_t>(), (size_t)n * ix->tp, grid[0], s));
     ix->stats.launches += 1;
     // visited bitmap, one row of ceil(n / 32) words per root slot; cleared once
     // here, then lazily after each batch (only the words the batch set)
     const uint32_t NW = (n + 31) / 32;
-    DevMem m_vis, m_ht, m_htoff, m_itemp, m_bits, m_cand, m_candc, m_out, m_sorted, m_keep, m_temp;
+    PoolMem m_vis(s), m_ht(s), m_htoff(s), m_itemp(s), m_bits(s), m_cand(s), m_candc(s), m_out(s),
+        m_sorted(s), m_keep(s), m_temp(s);
     PLL_CHECK(m_vis.alloc((size_t)bmax * NW * 4));
     PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)bmax * NW * 4, s));
     const TestCaps caps = test_caps();
@@ -162,18 +169,22 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     const size_t itemp_bytes = ((batch_init_temp_bytes(bmax) + 255) & ~(size_t)255) + ((size_t)bmax + 1) * 8 + 256;
     PLL_CHECK(m_itemp.alloc(itemp_bytes));
     PLL_CHECK(m_bits.alloc((size_t)bmax * 16));
-    DevMem m_filt;
+    PoolMem m_filt(s);
     PLL_CHECK(m_filt.alloc((size_t)bmax * FILT_WORDS * 4));
     uint64_t cand_cap = caps.cand ? caps.cand : std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
     uint64_t out_cap = caps.out ? caps.out : std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
     size_t temp_bytes = 0;
     const int end_bit = 32 + std::max(1, bit_length(n - 1));
+    // the distance byte is no sort key: a root's BFS labels a vertex at most
+    // once (one visited bit per root and vertex), so (u, k) is unique within
+    // a batch and the order by (u, k) is the whole order
+    constexpr int SORT_BEGIN_BIT = 8;
     auto alloc_out = [&]() -> int {
         PLL_CHECK(m_out.alloc(out_cap * 8));
         PLL_CHECK(m_sorted.alloc(out_cap * 8));
         PLL_CHECK(m_keep.alloc(out_cap));
         size_t a = 0, b = 0;
-        PLL_CHECK(labels_sort_tuples(nullptr, nullptr, out_cap, end_bit, nullptr, &a, s));
+        PLL_CHECK(labels_sort_tuples(nullptr, nullptr, out_cap, SORT_BEGIN_BIT, end_bit, nullptr, &a, s));
         PLL_CHECK(labels_compact(nullptr, nullptr, out_cap, nullptr, nullptr, nullptr, &b, s));
         temp_bytes = std::max(a, b);
         PLL_CHECK(m_temp.alloc(temp_bytes));
@@ -201,24 +212,23 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         PLL_TRY(cudaStreamSynchronize(s));
         return PLL_OK;
     };
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    PLL_TRY(cudaEventCreate(&ev0));
-    PLL_TRY(cudaEventCreate(&ev1));
-    cudaEvent_t sweep_ev[16] = {};
-    for (auto &e : sweep_ev) PLL_TRY(cudaEventCreate(&e));
+    // ev[0..1]: a batch's BFS part (init, levels, reset); ev[2..3]: its
+    // sort, cleanup, compaction and append; sweep_ev: the level sweeps
+    cudaEvent_t ev[4] = {}, sweep_ev[16] = {};
     struct EvGuard {
-        cudaEvent_t a, b;
-        cudaEvent_t *sw;
+        cudaEvent_t *a, *sw;
         ~EvGuard() {
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
+            for (int i = 0; i < 4; ++i) if (a[i]) cudaEventDestroy(a[i]);
             for (int i = 0; i < 16; ++i) if (sw[i]) cudaEventDestroy(sw[i]);
         }
-    } ev_guard{ev0, ev1, sweep_ev};
+    } ev_guard{ev, sweep_ev};
+    for (auto &e : ev) PLL_TRY(cudaEventCreate(&e));
+    for (auto &e : sweep_ev) PLL_TRY(cudaEventCreate(&e));
+    cudaEvent_t ev0 = ev[0], ev1 = ev[1];
 
     // the level loop as a CUDA graph: instantiated once, launched per batch
     // after the batch's arguments are copied in
-    DevMem m_args;
+    PoolMem m_args(s);
     cudaGraph_t lgraph = nullptr;
     cudaGraphExec_t lexec = nullptr;
     struct GraphGuard {
@@ -235,6 +245,21 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     }
 
     uint64_t total = 0, pre = 0, batches = 0;
+    // A batch's sort, cleanup, compaction and append are not waited for: the
+    // next batch is enqueued right behind them, and its first read-back
+    // brings the kept count and the appends' error word (neither is touched
+    // by a batch's BFS) along with its own counters.
+    bool post_pending = false;
+    auto settle_post = [&]() -> int {
+        if (!post_pending) return PLL_OK;
+        post_pending = false;
+        if (h->c.err_post & ERR_POOL) return PLL_E_NOMEM;
+        total += h->c.nkept;
+        float ms = 0;
+        PLL_TRY(cudaEventElapsedTime(&ms, ev[2], ev[3]));
+        ix->stats.ms_post += ms;
+        return PLL_OK;
+    };
     uint32_t k0 = 0, B = std::min<uint32_t>(64, bmax);
     uint64_t last_cand = 0, last_out = 0, last_B = 1;
     unsigned long long work0[4] = {0, 0, 0, 0};
@@ -319,6 +344,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         ix->stats.launches += 1;
         PLL_TRY(cudaEventRecord(ev1, s));
         PLL_CHECK(read_back());
+        PLL_CHECK(settle_post());
         {
             float ms = 0;
             PLL_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
@@ -374,8 +400,9 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
                 ix->stats.launches += 3;
                 ix->stats.cub_calls += 1;
             }
+            PLL_TRY(cudaEventRecord(ev[2], s));
             size_t tb = temp_bytes;
-            PLL_CHECK(labels_sort_tuples(m_out.as<uint64_t>(), m_sorted.as<uint64_t>(), P, end_bit,
+            PLL_CHECK(labels_sort_tuples(m_out.as<uint64_t>(), m_sorted.as<uint64_t>(), P, SORT_BEGIN_BIT, end_bit,
                                          m_temp.p, &tb, s));
             // the sort is done with the temporary space; the cleanup borrows it
             PLL_CHECK(labels_cleanup(m_sorted.as<uint64_t>(), P, m_keep.as<uint8_t>(), k0, k1 - k0,
@@ -383,17 +410,20 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
             tb = temp_bytes;
             PLL_CHECK(labels_compact(m_sorted.as<uint64_t>(), m_keep.as<uint8_t>(), P,
                                      m_out.as<uint64_t>(), &d_ctr->nkept, m_temp.p, &tb, s));
-            PLL_CHECK(labels_append(st, m_out.as<uint64_t>(), &d_ctr->nkept, P, &d_ctr->err, s));
+            PLL_CHECK(labels_append(st, m_out.as<uint64_t>(), &d_ctr->nkept, P, &d_ctr->err_post, s));
             ix->stats.launches += 2;   // cleanup, append
             ix->stats.cub_calls += 2;  // sort, select
-            PLL_CHECK(read_back());
-            if (h->c.err & ERR_POOL) return PLL_E_NOMEM;
-            total += h->c.nkept;
+            PLL_TRY(cudaEventRecord(ev[3], s));
+            post_pending = true;
         }
-        for (int w = 0; w < 4; ++w) work0[w] = h->c.work[w];
+        for (int w = 0; w < 4; ++w) work0[w] = h->c.work[w];  // the sweeps' counts so far
         ++batches;
         k0 = k1;
         B = std::min<uint32_t>(B * 2, bmax);
+    }
+    if (post_pending) {
+        PLL_CHECK(read_back());
+        PLL_CHECK(settle_post());
     }
     if (device_levels || graph_levels) {  // phase times and level counts of the device-side loop
         LoopState ls{};
@@ -418,7 +448,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     PLL_TRY(dev_malloc(&ix->d_lab, std::max<uint64_t>(total, 1) * 4));
     size_t ftb = 0;
     PLL_CHECK(labels_finalize(st, total, ix->d_lab_off, ix->d_lab, nullptr, &ftb, s));
-    DevMem ftemp;
+    PoolMem ftemp(s);
     PLL_CHECK(ftemp.alloc(ftb));
     Timer tf(s);
     tf.start();
@@ -482,10 +512,15 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     ix->stats.t = o.t;
     ix->stats.nnz = nnz;
     Timer tm(s);
+    const cudaMemPool_t spool = scratch_pool();
+    if (spool) {  // the build's scratch peak, from here on
+        uint64_t zero = 0;
+        (void)cudaMemPoolSetAttribute(spool, cudaMemPoolAttrUsedMemHigh, &zero);
+    }
 
     // ---- 1. checks, order, relabel
     tm.start();
-    DevMem m_err;
+    PoolMem m_err(s);
     PLL_CHECK(m_err.alloc(4));
     uint32_t *d_err = m_err.as<uint32_t>();
     uint32_t h_err = 0;
@@ -497,7 +532,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     if (h_err) return PLL_E_INVAL;
     PLL_TRY(dev_malloc(&ix->d_order, std::max<size_t>((size_t)n * 4, 4)));
     PLL_TRY(dev_malloc(&ix->d_inv, std::max<size_t>((size_t)n * 4, 4)));
-    DevMem m_gs, m_gof, m_local;
+    PoolMem m_gs(s), m_gof(s), m_local(s);
     if (batch) {  // each graph's own Degree order, graphs interleaved by local rank
         PLL_CHECK(m_gs.alloc(((size_t)graphs + 1) * 4));
         PLL_CHECK(m_gof.alloc(std::max<size_t>((size_t)n * 4, 4)));
@@ -515,7 +550,7 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     } else {
         PLL_CHECK(prep_degree_order(g, ix->d_order, s));
     }
-    DevMem m_roff, m_rcol, m_inX;
+    PoolMem m_roff(s), m_rcol(s), m_inX(s);
     PLL_CHECK(m_roff.alloc(((size_t)n + 1) * 4));
     PLL_CHECK(m_rcol.alloc(std::max<uint64_t>(nnz, 1) * 4));
     PLL_CHECK(prep_relabel(g, ix->d_order, ix->d_inv, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), s));
@@ -566,6 +601,12 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     PLL_CHECK(pruned_stage(ix, m_roff.as<uint32_t>(), m_rcol.as<uint32_t>(), m_inX.as<uint8_t>(),
                            bmax, block, o.flags, s));
     ix->stats.ms_pruned = tm.stop_ms();
+    if (spool) {
+        uint64_t high = 0;
+        if (cudaMemPoolGetAttribute(spool, cudaMemPoolAttrUsedMemHigh, &high) == cudaSuccess)
+            ix->stats.scratch_peak_bytes = high;
+        (void)cudaGetLastError();
+    }
 
     PLL_TRY(dev_malloc(&ix->d_qerr, 16));
     PLL_TRY(cudaMemsetAsync(ix->d_qerr, 0, 16, s));
@@ -578,18 +619,74 @@ int build_device(const uint32_t *off, const uint32_t *col, uint32_t n, uint64_t 
     return PLL_OK;
 }
 
-// temporary device copy of a host array, stream ordered
-struct AsyncBuf {
-    void *p = nullptr;
-    cudaStream_t s;
-    explicit AsyncBuf(cudaStream_t st) : s(st) {}
-    ~AsyncBuf() { if (p) cudaFreeAsync(p, s); }
-    int alloc(size_t b) {
-        cudaError_t e = cudaMallocAsync(&p, b ? b : 16, s);
-        if (e != cudaSuccess) { p = nullptr; (void)cudaGetLastError(); return PLL_E_NOMEM; }
-        return PLL_OK;
+}  // namespace
+
+// The scratch pool: every temporary of a build and the staging copies of the
+// host-pointer entry points are allocated from it in stream order. The
+// default pool hands freed memory back at every synchronisation, and a
+// cudaMalloc / cudaFree pair maps and unmaps pages synchronously (about 3 ms
+// per GiB, and a build needs a few GiB of scratch); this pool keeps up to
+// an eighth of the device's memory mapped between calls (only what calls
+// actually used), until pll_release_cached. One pool per CUDA context, found
+// by the context's unique id (a context destroyed by a device reset takes its
+// pool with it and is never asked for it again).
+
+namespace {
+std::mutex g_pool_mu;
+struct PoolEntry { unsigned long long ctx_id; cudaMemPool_t pool; };
+std::vector<PoolEntry> g_pools;
+
+// unique id of the current context (false if there is none or the driver
+// cannot say)
+bool current_ctx_id(unsigned long long *id) {
+    static PFN_cuCtxGetCurrent_v4000 get_ctx = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void **>(&get_ctx), 4000,
+                                             cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void **>(&get_id), 12000,
+                                             cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            get_ctx = nullptr;
+            get_id = nullptr;
+        }
     }
-};
+    CUcontext ctx = nullptr;
+    return get_ctx && get_id && get_ctx(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, id) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaMemPool_t scratch_pool() {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return nullptr;
+    for (const PoolEntry &e : g_pools)
+        if (e.ctx_id == id) return e.pool;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { (void)cudaGetLastError(); total_b = 8ull << 33; }
+    uint64_t keep = total_b / 8;
+    (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools.push_back({id, pool});
+    return pool;
+}
+
+namespace {
+
+// temporary device copy of a host array, stream ordered
+using AsyncBuf = PoolMem;
 
 int query_status(const pll_index *ix, cudaStream_t s) {
     // the two counters come back into pinned memory (a pageable target makes
@@ -655,6 +752,18 @@ TestCaps test_caps() {
 using namespace pll;
 
 extern "C" {
+
+PLL_API int pll_release_cached(void) {
+    using namespace pll;
+    cudaError_t e = cudaDeviceSynchronize();  // frees in flight complete first
+    if (e != cudaSuccess) return cuda_status(e);
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return PLL_OK;
+    for (const PoolEntry &pe : g_pools)
+        if (pe.ctx_id == id && (e = cudaMemPoolTrimTo(pe.pool, 0)) != cudaSuccess) return cuda_status(e);
+    return PLL_OK;
+}
 
 PLL_API const char *pll_status_str(int status) {
     switch (status) {

@@ -480,10 +480,10 @@ int directed_labels(pll_dindex *ix, DevMem *adj_off, DevMem *adj_col, uint32_t b
             PLL_CHECK(ensure(S[dir], std::max<uint64_t>(P[dir], 1) * 8, 0, s));
             if (P[dir] == 0) continue;
             size_t tb = 0;
-            PLL_CHECK(labels_sort_tuples(T[dir].as<uint64_t>(), S[dir].as<uint64_t>(), P[dir], 64, nullptr, &tb, s));
+            PLL_CHECK(labels_sort_tuples(T[dir].as<uint64_t>(), S[dir].as<uint64_t>(), P[dir], 0, 64, nullptr, &tb, s));
             PLL_CHECK(ensure(temp, tb, 0, s));
             tb = temp.bytes;
-            PLL_CHECK(labels_sort_tuples(T[dir].as<uint64_t>(), S[dir].as<uint64_t>(), P[dir], 64, temp.p, &tb, s));
+            PLL_CHECK(labels_sort_tuples(T[dir].as<uint64_t>(), S[dir].as<uint64_t>(), P[dir], 0, 64, temp.p, &tb, s));
         }
         for (int dir = 0; dir < 2; ++dir) {
             if (P[dir] == 0) continue;

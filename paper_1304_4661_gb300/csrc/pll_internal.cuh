@@ -129,6 +129,54 @@ inline void host_free(void *p) {
     alloc_note(-1);
 }
 
+// The library's stream-ordered memory pool of the current CUDA context
+// (pll_abi.cu), which keeps freed memory mapped for later calls; nullptr if
+// the driver cannot name the context (the default pool is used then).
+cudaMemPool_t scratch_pool();
+// Stream-ordered scratch from that pool (counted and failed like dev_malloc).
+template <class T> inline cudaError_t pool_malloc(T **p, size_t b, cudaStream_t s) {
+    *p = nullptr;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    void *q = nullptr;
+    const cudaMemPool_t pool = scratch_pool();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, b ? b : 16, pool, s)
+                               : cudaMallocAsync(&q, b ? b : 16, s);
+    if (e == cudaSuccess) { *p = static_cast<T *>(q); alloc_note(1); }
+    return e;
+}
+inline void pool_free(void *p, cudaStream_t s) {
+    if (!p) return;
+    cudaFreeAsync(p, s);
+    alloc_note(-1);
+}
+// Scratch of one call: freed in stream order on its stream when it goes out
+// of scope, so no host wait and no unmapping; release() hands ownership out
+// (the new owner frees it with pool_free on the same stream).
+struct PoolMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s;
+    explicit PoolMem(cudaStream_t st) : s(st) {}
+    PoolMem(const PoolMem &) = delete;
+    PoolMem &operator=(const PoolMem &) = delete;
+    ~PoolMem() { reset(); }
+    int alloc(size_t b) {
+        reset();
+        if (b == 0) b = 16;
+        const cudaError_t e = pool_malloc(&p, b, s);
+        if (e != cudaSuccess) { p = nullptr; (void)cudaGetLastError(); return PLL_E_NOMEM; }
+        bytes = b;
+        return PLL_OK;
+    }
+    void reset() {
+        pool_free(p, s);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    void *release() { void *q = p; p = nullptr; bytes = 0; return q; }
+};
+
 // Device allocation that frees itself; release() hands ownership out (the
 // new owner frees it with dev_free).
 struct DevMem {
@@ -216,8 +264,8 @@ struct BatchCounters {
                                   // claimed (cumulative)
     unsigned long long nkept;     // entries kept by the cleanup
     unsigned long long pool_top;  // label pool bump pointer
-    uint32_t err;
-    uint32_t pad;
+    uint32_t err;                 // errors of the batch's BFS (reset per batch)
+    uint32_t err_post;            // errors of the appends (never reset)
 };
 constexpr uint32_t ERR_TABLE = 1u << 5;    // root hash-table pool too small
 constexpr uint32_t ERR_TIMEOUT = 1u << 6;  // a grid barrier waited past its limit
@@ -297,8 +345,10 @@ struct LabelStore {
     uint32_t *pool = nullptr;
     uint64_t pool_cap = 0;
     unsigned long long *pool_top = nullptr;
+    bool pooled = false;  // `pool` comes from pool_malloc (else dev_malloc)
 };
-int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int end_bit,
+// radix sort of packed tuples by their bits [begin_bit, end_bit)
+int labels_sort_tuples(uint64_t *d_in, uint64_t *d_out, uint64_t count, int begin_bit, int end_bit,
                        void *d_temp, size_t *temp_bytes, cudaStream_t s);
 // scratch (>= 16 B bytes, may be NULL) holds each root's own tuple range
 int labels_cleanup(const uint64_t *d_sorted, uint64_t count, uint8_t *d_keep, uint32_t k0, uint32_t B,

@@ -32,7 +32,7 @@ SYMBOLS = [
     "pll_mlp_set_params", "pll_mlp_get_params", "pll_mlp_forward", "pll_mlp_grad",
     "pll_mlp_read_grad", "pll_mlp_adam", "pll_mlp_train_step", "pll_learned_order",
     "pll_save", "pll_load", "pll_test_fail_alloc", "pll_test_live_allocs", "pll_test_capacities",
-    "pll_test_barrier_timeout",
+    "pll_test_barrier_timeout", "pll_release_cached",
     "pll_paths_create", "pll_paths_parents", "pll_path_offsets", "pll_path_query",
     "pll_paths_free",
     "pll_build_directed", "pll_dquery", "pll_dlabel_entries", "pll_dexport_labels",
@@ -67,7 +67,8 @@ class Stats(C.Structure):
                 ("candidates", C.c_uint64), ("graphs", C.c_uint32), ("reserved32", C.c_uint32),
                 ("redone_batches", C.c_uint64), ("pool_regrows", C.c_uint64),
                 ("table_fallbacks", C.c_uint64), ("levels_launches", C.c_uint64),
-                ("ms_levels", C.c_double)]
+                ("ms_levels", C.c_double), ("ms_post", C.c_double),
+                ("scratch_peak_bytes", C.c_uint64)]
 
 
 class ServerOpts(C.Structure):
@@ -206,8 +207,16 @@ def load(build_if_missing: bool = True):
     lib.pll_test_capacities.argtypes = [C.c_uint64] * 4
     lib.pll_test_barrier_timeout.restype = None
     lib.pll_test_barrier_timeout.argtypes = [C.c_uint64]
+    lib.pll_release_cached.restype = i32
+    lib.pll_release_cached.argtypes = []
     _lib = lib
     return lib
+
+
+def release_cached():
+    """pll_release_cached: hand the current context's cached scratch memory
+    back to the driver (synchronises the current device)."""
+    _check(load().pll_release_cached(), "pll_release_cached")
 
 
 def status_str(code: int) -> str:

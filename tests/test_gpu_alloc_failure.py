@@ -41,3 +41,22 @@ def test_every_allocation_failure_is_clean(t):
     assert same_labels(ix.labels(), ref.labels())
     ix.close()
     assert lib.pll_test_live_allocs() == base
+
+
+def test_release_cached_scratch_then_build_again():
+    """Scratch comes from the library's pool, which keeps freed memory mapped
+    between builds; pll_release_cached hands it back. Builds before and after
+    give the oracle's labels, and no allocation is left behind."""
+    import torch
+    lib = pll.load()
+    g = gg.ba(3000, 3, 5)
+    off, col = dev_u32(g.offsets), dev_u32(g.cols)
+    ref = oracle.Index(g.offsets, g.cols, 16).labels()
+    base = lib.pll_test_live_allocs()
+    for _ in range(2):
+        ix = pll.Index.build(off, col, t=16)
+        assert same_labels(ix.labels(), ref)
+        ix.close()
+        assert lib.pll_test_live_allocs() == base
+        pll.release_cached()
+    torch.cuda.synchronize()
