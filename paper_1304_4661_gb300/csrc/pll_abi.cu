@@ -121,7 +121,7 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     st.off = m_off.as<uint64_t>();
     st.len = m_len.as<uint32_t>();
     st.cap = m_cap.as<uint32_t>();
-    st.pool_cap = test_caps().pool ? test_caps().pool : std::max<uint64_t>((uint64_t)n * 16, 1ull << 22);
+    st.pool_cap = test_caps().pool ? test_caps().pool : std::max<uint64_t>((uint64_t)n * 64, 1ull << 22);
     PLL_CHECK(m_pool.alloc(st.pool_cap * 4));
     st.pool = m_pool.as<uint32_t>();
     st.pooled = true;
@@ -163,7 +163,17 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     PLL_CHECK(m_vis.alloc((size_t)bmax * NW * 4));
     PLL_TRY(cudaMemsetAsync(m_vis.p, 0, (size_t)bmax * NW * 4, s));
     const TestCaps caps = test_caps();
-    uint64_t ht_cap = caps.ht ? caps.ht : std::max<uint64_t>((uint64_t)bmax * 128, 1ull << 20);
+    // Initial sizes generous enough that the first large root batches do not
+    // overflow (a batch that overflows runs again; roots whose tables do not
+    // fit are binary-searched): scratch comes from the pool, so a large buffer
+    // costs memory but no mapping time. The candidate and tuple buffers, the
+    // two largest, take at most a sixteenth of the free memory each.
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_b = 0;
+    }
+    uint64_t ht_cap = caps.ht ? caps.ht : std::max<uint64_t>((uint64_t)bmax * 2048, 1ull << 20);
     PLL_CHECK(m_ht.alloc(ht_cap * 4));
     PLL_CHECK(m_htoff.alloc(((size_t)bmax + 1) * 8));
     const size_t itemp_bytes = ((batch_init_temp_bytes(bmax) + 255) & ~(size_t)255) + ((size_t)bmax + 1) * 8 + 256;
@@ -171,8 +181,12 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
     PLL_CHECK(m_bits.alloc((size_t)bmax * 16));
     PoolMem m_filt(s);
     PLL_CHECK(m_filt.alloc((size_t)bmax * FILT_WORDS * 4));
-    uint64_t cand_cap = caps.cand ? caps.cand : std::max<uint64_t>((uint64_t)n * 16, 1ull << 24);
-    uint64_t out_cap = caps.out ? caps.out : std::max<uint64_t>((uint64_t)n * 4, 1ull << 22);
+    uint64_t cand_cap = caps.cand ? caps.cand
+                                  : std::max<uint64_t>(std::min<uint64_t>((uint64_t)n * 256, free_b / 16 / 24),
+                                                       1ull << 24);
+    uint64_t out_cap = caps.out ? caps.out
+                                : std::max<uint64_t>(std::min<uint64_t>((uint64_t)n * 64, free_b / 16 / 17),
+                                                     1ull << 22);
     size_t temp_bytes = 0;
     const int end_bit = 32 + std::max(1, bit_length(n - 1));
     // the distance byte is no sort key: a root's BFS labels a vertex at most
