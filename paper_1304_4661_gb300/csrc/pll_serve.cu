@@ -42,23 +42,21 @@
 
 #include "pll_internal.cuh"
 #include "serve_ring.h"
+#include "serve_sync.h"
 
 // Locking. Every request passes through three hands (its client, the
 // dispatcher, its waiter), so no lock is held across a sleep and none is
 // shared by all of them:
-//   * the ring (admission, the FIFO of live requests, the stream slots'
-//     bookkeeping, the statistics) is guarded by a spin lock held for a few
-//     dozen instructions: a contended hand-off is a cache-line transfer, not a
-//     futex sleep and wake-up, which would cap the whole server at one
-//     request per wake-up latency;
+//   * the ring (admission, the FIFO of live requests, the statistics) is
+//     guarded by a spin lock held for a few dozen instructions: a contended
+//     hand-off is a cache-line transfer, not a futex sleep and wake-up, which
+//     would cap the whole server at one request per wake-up latency;
 //   * tickets live in 64 shards, each with its own mutex;
-//   * completion is a per-request flag; a waiter spins on it for a while and
-//     only then sleeps on its shard's condition variable, which the
-//     dispatcher signals only when someone sleeps there.
-// Sleeping on a condition variable (a full ring, an idle dispatcher, a
-// waiter) always re-checks its condition under the mutex after announcing
-// itself in a counter, and the other side reads that counter after making
-// the condition true (both sequentially consistent), so no wake-up is lost.
+//   * completion is a per-request flag; a waiter polls it for a while and
+//     only then sleeps on its shard's SleepSlot, which the dispatcher
+//     signals only when someone sleeps there.
+// A full ring and an idle dispatcher sleep on SleepSlots too; serve_sync.h
+// states why no wake-up is lost.
 
 namespace {
 
@@ -89,39 +87,18 @@ struct Slot {
     bool busy = false;  // dispatcher thread only
 };
 
-class SpinLock {
-    std::atomic<bool> held_{false};
-
-  public:
-    void lock() {
-        for (unsigned spins = 0;;) {
-            if (!held_.exchange(true, std::memory_order_acquire)) return;
-            while (held_.load(std::memory_order_relaxed))
-                if (++spins > 256) std::this_thread::yield();
-        }
-    }
-    void unlock() { held_.store(false, std::memory_order_release); }
-};
+using pll::SleepSlot;
+using pll::SpinLock;
 
 struct alignas(64) Shard {
-    std::mutex mu;
-    std::condition_variable cv;
+    SleepSlot slot;  // its mutex also guards the map
     std::unordered_map<uint64_t, Request *> map;
-    std::atomic<int> sleepers{0};
 };
 
 constexpr int SHARDS = 64;
 
 double us_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::micro>(b - a).count();
-}
-
-// Wake whoever sleeps on (mu, cv) after `count` announced itself; the caller
-// has already made the awaited condition true.
-void wake(std::mutex &mu, std::condition_variable &cv, const std::atomic<int> &count) {
-    if (count.load(std::memory_order_seq_cst) == 0) return;
-    { std::lock_guard<std::mutex> lock(mu); }
-    cv.notify_all();
 }
 
 }  // namespace
@@ -148,9 +125,7 @@ struct pll_server {
     // ---- tickets
     Shard shards[SHARDS];
     // ---- sleeping: a full ring (clients), an idle dispatcher
-    std::mutex space_mu, work_mu;
-    std::condition_variable cv_space, cv_work;
-    std::atomic<int> space_sleepers{0}, work_sleepers{0};
+    SleepSlot space, work;
     std::atomic<bool> stop{false};
     std::thread worker;
     std::atomic<unsigned long long> pack_ns{0};  // client staging time (no lock)
@@ -201,14 +176,14 @@ void retire_run(pll_server *sv, const Run &r, int status) {
     sv->st.unpack_us += us_between(t0, now);
     sv->st.device_us = sv->device_us;
     sv->ring.unlock();
-    wake(sv->space_mu, sv->cv_space, sv->space_sleepers);
+    sv->space.wake();
     for (Request *q : r.reqs) {
         if (q->ticket == 0) { delete q; continue; }
         Shard &sh = sv->shard(q->ticket);
         q->latency_us = us_between(q->t_submit, now);
         q->status = status;
         q->done.store(true, std::memory_order_seq_cst);  // q may be gone after this
-        wake(sh.mu, sh.cv, sh.sleepers);
+        sh.slot.wake();
     }
 }
 
@@ -279,15 +254,13 @@ void worker_loop(pll_server *sv) {
             sv->ring.unlock();
             if (idle && !ready) {
                 if (sv->stop.load(std::memory_order_seq_cst) && empty) return;
-                if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US)) {
-                    std::unique_lock<std::mutex> lock(sv->work_mu);
-                    sv->work_sleepers.fetch_add(1, std::memory_order_seq_cst);
-                    sv->cv_work.wait_for(lock, std::chrono::milliseconds(2), [&] {
-                        return sv->stop.load(std::memory_order_seq_cst) ||
-                               sv->staged_seq.load(std::memory_order_seq_cst) != seq;
-                    });
-                    sv->work_sleepers.fetch_sub(1, std::memory_order_seq_cst);
-                }
+                if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US))
+                    sv->work.wait_until(
+                        [&] {
+                            return sv->stop.load(std::memory_order_seq_cst) ||
+                                   sv->staged_seq.load(std::memory_order_seq_cst) != seq;
+                        },
+                        Clock::now() + std::chrono::milliseconds(2));
                 continue;
             }
         }
@@ -408,17 +381,14 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
             return ok;
         };
         if (try_admit()) break;
-        std::unique_lock<std::mutex> lock(sv->space_mu);
-        sv->space_sleepers.fetch_add(1, std::memory_order_seq_cst);
-        admitted = try_admit();
-        if (!admitted)
-            sv->cv_space.wait_for(lock, std::chrono::milliseconds(10));
-        sv->space_sleepers.fetch_sub(1, std::memory_order_seq_cst);
+        sv->space.wait_until(
+            [&] { return sv->stop.load(std::memory_order_seq_cst) || (admitted = try_admit()); },
+            Clock::now() + std::chrono::milliseconds(10));
     }
     const uint64_t tk = r->ticket;
     Shard &sh = sv->shard(tk);
     {
-        std::lock_guard<std::mutex> lock(sh.mu);
+        std::lock_guard<std::mutex> lock(sh.slot.mu);
         sh.map[tk] = r;
     }
     // stage the pairs into the request's own slots, checking the ids on the way
@@ -433,14 +403,14 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
         h[2 * i + 1] = b < n ? b : 0;
     }
     if (bad) {  // keeps its slots until its run retires, answers nobody
-        std::lock_guard<std::mutex> lock(sh.mu);
+        std::lock_guard<std::mutex> lock(sh.slot.mu);
         sh.map.erase(tk);
         r->ticket = 0;
     }
     sv->pack_ns.fetch_add((unsigned long long)(us_between(t0, Clock::now()) * 1e3), std::memory_order_relaxed);
     r->staged.store(true, std::memory_order_release);  // pairs and ticket before the flag
     sv->staged_seq.fetch_add(1, std::memory_order_seq_cst);
-    wake(sv->work_mu, sv->cv_work, sv->work_sleepers);
+    sv->work.wake();
     if (bad) return PLL_E_INVAL;
     *ticket = tk;
     return PLL_OK;
@@ -452,7 +422,7 @@ PLL_API int pll_server_wait(pll_server *sv, uint64_t ticket, int64_t timeout_us,
     Request *r = nullptr;
     bool finished = false;
     {
-        std::lock_guard<std::mutex> lock(sh.mu);
+        std::lock_guard<std::mutex> lock(sh.slot.mu);
         auto it = sh.map.find(ticket);
         if (it == sh.map.end() || it->second->waiting) return PLL_E_INVAL;
         r = it->second;
@@ -475,13 +445,11 @@ PLL_API int pll_server_wait(pll_server *sv, uint64_t ticket, int64_t timeout_us,
         const int64_t spin = timeout_us < 0 ? SPIN_US : std::min<int64_t>(SPIN_US, timeout_us);
         while (!done() && Clock::now() - t0 < std::chrono::microseconds(spin)) std::this_thread::yield();
         if (!done()) {
-            std::unique_lock<std::mutex> lock(sh.mu);
-            sh.sleepers.fetch_add(1, std::memory_order_seq_cst);
             bool ok = true;
-            if (timeout_us < 0) sh.cv.wait(lock, done);
-            else ok = sh.cv.wait_until(lock, t0 + std::chrono::microseconds(timeout_us), done);
-            sh.sleepers.fetch_sub(1, std::memory_order_seq_cst);
+            if (timeout_us < 0) sh.slot.wait(done);
+            else ok = sh.slot.wait_until(done, t0 + std::chrono::microseconds(timeout_us));
             if (!ok) {
+                std::lock_guard<std::mutex> lock(sh.slot.mu);
                 r->waiting = false;
                 return PLL_E_TIMEOUT;
             }
@@ -490,7 +458,7 @@ PLL_API int pll_server_wait(pll_server *sv, uint64_t ticket, int64_t timeout_us,
     if (latency_us) *latency_us = r->latency_us;
     const int s = r->status;
     {
-        std::lock_guard<std::mutex> lock(sh.mu);
+        std::lock_guard<std::mutex> lock(sh.slot.mu);
         sh.map.erase(ticket);
     }
     delete r;
@@ -575,10 +543,8 @@ PLL_API int pll_server_get_stats(pll_server *sv, pll_server_stats *out) {
 PLL_API int pll_server_stop(pll_server *sv) {
     if (!sv) return PLL_OK;
     sv->stop.store(true, std::memory_order_seq_cst);
-    { std::lock_guard<std::mutex> lock(sv->work_mu); }
-    sv->cv_work.notify_all();
-    { std::lock_guard<std::mutex> lock(sv->space_mu); }
-    sv->cv_space.notify_all();
+    sv->work.wake();
+    sv->space.wake();
     if (sv->worker.joinable()) sv->worker.join();
     const int s = sv->fatal;
     destroy(sv);
