@@ -117,7 +117,8 @@ typedef struct pll_stats {
     uint64_t pruned_masks;       /* bit-parallel mask pairs read by prune tests */
     uint64_t pruned_expanded;    /* arcs scanned from unpruned vertices */
     uint64_t launches;           /* kernels of this library launched by the build
-                                    (not counting CUB's) */
+                                    (not counting CUB's; the kernels a CUDA
+                                    graph runs are counted one by one) */
     uint64_t cub_calls;          /* CUB device-wide sorts, scans, selects */
     /* the two sweeps of the pruned stage, CUDA-event time summed over launches */
     double ms_expand;            /* expand sweeps (claim + distance check) */

@@ -447,6 +447,8 @@ int pruned_stage(pll_index *ix, const uint32_t *roff, const uint32_t *rcol, cons
         ix->stats.ms_test = ls.ns_test * 1e-6;
         ix->stats.expand_launches = ls.levels;
         ix->stats.test_launches = ls.levels;
+        // the graph's body runs four kernels a level (expand, step, test, step)
+        if (graph_levels) ix->stats.launches += 4ull * ls.levels;
     }
     ix->stats.pruned_scanned = h->c.work[0];
     ix->stats.pruned_masks = h->c.work[1];
