@@ -7,15 +7,19 @@
 // Memory. The server owns one ring of P pair slots in pinned, mapped host
 // memory that the GPU reads and writes directly (over NVLink-C2C on a GB300;
 // no copies): pairs (s, t) as 8 bytes each, results as 1 byte each, 9 P bytes
-// in all (pool_bytes). A request of q pairs
-// is ADMITTED when q contiguous slots are free: pll_server_submit blocks until
-// then, so at most P pairs are ever queued or in flight. The client's own
-// thread copies its pairs into its slots (checking every id on the way); the
-// slots stay held until the request's results are back.
+// in all (pool_bytes). A large ring is cut into up to four parts, each with
+// its own lock and FIFO, and a client thread always uses the same part, so
+// that clients admitting requests at once rarely meet on one lock. A request
+// of q pairs is ADMITTED when q contiguous slots of its part are free:
+// pll_server_submit blocks until then, so at most P pairs are ever queued or
+// in flight. The client's own thread copies its pairs into its slots
+// (checking every id on the way); the slots stay held until the request's
+// results are back.
 //
 // Continuous batching. One dispatcher thread takes, whenever one of `streams`
 // stream slots is free, the longest run of staged requests that are waiting
-// (arrival order, contiguous in the ring, at most max_batch_pairs pairs) and
+// in a part (arrival order, contiguous in the ring, at most max_batch_pairs
+// pairs; the parts in turn) and
 // launches it as one unit on that slot's stream: one query launch (k_query,
 // reading the run's interleaved pairs in place from the ring and writing its
 // results into the ring) between two events.
@@ -47,10 +51,11 @@
 // Locking. Every request passes through three hands (its client, the
 // dispatcher, its waiter), so no lock is held across a sleep and none is
 // shared by all of them:
-//   * the ring (admission, the FIFO of live requests, the statistics) is
-//     guarded by a spin lock held for a few dozen instructions: a contended
-//     hand-off is a cache-line transfer, not a futex sleep and wake-up, which
-//     would cap the whole server at one request per wake-up latency;
+//   * each part of the ring (admission, its FIFO of live requests, its
+//     statistics) is guarded by a spin lock held for a few dozen
+//     instructions: a contended hand-off is a cache-line transfer, not a
+//     futex sleep and wake-up, which would cap the whole server at one
+//     request per wake-up latency;
 //   * tickets live in 64 shards, each with its own mutex;
 //   * completion is a per-request flag; a waiter polls it for a while and
 //     only then sleeps on its shard's SleepSlot, which the dispatcher
@@ -77,7 +82,7 @@ struct Request {
 struct Run {
     std::vector<Request *> reqs;  // consecutive in the ring
     uint64_t off = 0, pairs = 0;
-    int slot = -1;
+    int slot = -1, part = 0;
     int fail = PLL_OK;  // a launch that failed: retired with this status, in order
 };
 
@@ -95,10 +100,34 @@ struct alignas(64) Shard {
     std::unordered_map<uint64_t, Request *> map;
 };
 
+// One part of the pair ring: slots [base, base + cap).
+struct alignas(64) RingPart {
+    SpinLock lock;                    // guards the fields up to `dispatch`
+    uint64_t base = 0, cap = 0;
+    std::deque<Request *> live;       // hold slots of this part, ring order
+    size_t nlaunched = 0;             // live[0, nlaunched) belong to launched runs
+    uint64_t next_seq = 0;            // tickets issued here: part + 1 + seq * parts
+    uint64_t requests = 0, pairs = 0, max_inflight_bytes = 0;
+    SleepSlot space;                  // clients waiting for free slots here
+    alignas(64) std::atomic<uint64_t> staged_seq{0};  // bumped by every staged request
+    // dispatcher thread only
+    uint64_t seen_seq = ~0ull;
+    bool leftover = false;            // staged requests a run did not take (size, wrap)
+};
+
 constexpr int SHARDS = 64;
+constexpr uint32_t MAX_PARTS = 4;
 
 double us_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+std::atomic<uint32_t> g_client_threads{0};
+
+// the part a client thread uses: threads are dealt out in turn
+uint32_t client_part(uint32_t parts) {
+    thread_local const uint32_t id = g_client_threads.fetch_add(1, std::memory_order_relaxed);
+    return id % parts;
 }
 
 }  // namespace
@@ -116,39 +145,50 @@ struct pll_server {
     std::vector<Slot> slots;
     std::deque<Run> inflight;         // dispatcher thread only, launch order
     double device_us = 0;             // dispatcher thread only
-    // ---- guarded by `ring`
-    SpinLock ring;
-    std::deque<Request *> live;       // hold ring slots, ring order
-    size_t nlaunched = 0;             // live[0, nlaunched) belong to launched runs
-    uint64_t next_ticket = 1;
+    uint32_t nparts = 1, next_part = 0;  // next_part: dispatcher only
+    std::unique_ptr<RingPart[]> parts;
+    // ---- the dispatcher's statistics (batches, sizes, times)
+    SpinLock stats_lock;
     pll_server_stats st{};
     // ---- tickets
     Shard shards[SHARDS];
-    // ---- sleeping: a full ring (clients), an idle dispatcher
-    SleepSlot space, work;
+    // ---- an idle dispatcher sleeps here
+    SleepSlot work;
     std::atomic<bool> stop{false};
     std::thread worker;
     std::atomic<unsigned long long> pack_ns{0};  // client staging time (no lock)
-    std::atomic<uint64_t> staged_seq{0};         // bumped by every staged request
     int fatal = PLL_OK;
 
     Shard &shard(uint64_t ticket) { return shards[ticket % SHARDS]; }
+    uint64_t staged_sum() const {
+        uint64_t x = 0;
+        for (uint32_t p = 0; p < nparts; ++p) x += parts[p].staged_seq.load(std::memory_order_seq_cst);
+        return x;
+    }
 };
 
 namespace {
 
-// Slots for q pairs in the FIFO ring of live requests (serve_ring.h).
-bool ring_alloc(const std::deque<Request *> &live, uint64_t cap, uint64_t q, uint64_t *off) {
-    if (live.empty()) return pll::ring_place(true, 0, 0, 0, cap, q, off);
-    return pll::ring_place(false, live.front()->off, live.back()->off, live.back()->off + live.back()->q,
-                           cap, q, off);
+// Slots for q pairs in a part's FIFO ring of live requests (serve_ring.h);
+// offsets are the ring's own.
+bool ring_alloc(const RingPart &rp, uint64_t q, uint64_t *off) {
+    uint64_t rel = 0;
+    bool ok;
+    if (rp.live.empty()) {
+        ok = pll::ring_place(true, 0, 0, 0, rp.cap, q, &rel);
+    } else {
+        const Request *f = rp.live.front(), *b = rp.live.back();
+        ok = pll::ring_place(false, f->off - rp.base, b->off - rp.base, b->off + b->q - rp.base, rp.cap, q, &rel);
+    }
+    *off = rp.base + rel;
+    return ok;
 }
 
-uint64_t ring_used(const std::deque<Request *> &live, uint64_t cap) {
-    if (live.empty()) return 0;
-    const uint64_t first = live.front()->off;
-    const uint64_t end = live.back()->off + live.back()->q;
-    return live.back()->off >= first ? end - first : cap - first + end;
+uint64_t ring_used(const RingPart &rp) {
+    if (rp.live.empty()) return 0;
+    const uint64_t first = rp.live.front()->off;
+    const uint64_t end = rp.live.back()->off + rp.live.back()->q;
+    return rp.live.back()->off >= first ? end - first : rp.cap - (first - end);
 }
 
 int launch_run(pll_server *sv, const Run &r) {
@@ -170,13 +210,16 @@ void retire_run(pll_server *sv, const Run &r, int status) {
             if (q->ticket) std::memcpy(q->out, sv->h_out + q->off, q->q);
     const Clock::time_point now = Clock::now();
     sv->slots[r.slot].busy = false;
-    sv->ring.lock();
-    for (size_t i = 0; i < r.reqs.size(); ++i) sv->live.pop_front();
-    sv->nlaunched -= r.reqs.size();
+    RingPart &rp = sv->parts[r.part];
+    rp.lock.lock();
+    for (size_t i = 0; i < r.reqs.size(); ++i) rp.live.pop_front();
+    rp.nlaunched -= r.reqs.size();
+    rp.lock.unlock();
+    sv->stats_lock.lock();
     sv->st.unpack_us += us_between(t0, now);
     sv->st.device_us = sv->device_us;
-    sv->ring.unlock();
-    sv->space.wake();
+    sv->stats_lock.unlock();
+    rp.space.wake();
     for (Request *q : r.reqs) {
         if (q->ticket == 0) { delete q; continue; }
         Shard &sh = sv->shard(q->ticket);
@@ -187,14 +230,34 @@ void retire_run(pll_server *sv, const Run &r, int status) {
     }
 }
 
+// The longest run of staged requests waiting at the head of a part (taken
+// out of the part's unlaunched requests); empty if the first is not staged.
+Run take_run(pll_server *sv, RingPart &rp) {
+    Run run;
+    rp.lock.lock();
+    if (rp.nlaunched < rp.live.size() && rp.live[rp.nlaunched]->staged.load(std::memory_order_acquire)) {
+        run.off = rp.live[rp.nlaunched]->off;
+        for (size_t i = rp.nlaunched; i < rp.live.size(); ++i) {
+            Request *q = rp.live[i];
+            if (!q->staged.load(std::memory_order_acquire) || q->off != run.off + run.pairs)
+                break;  // not staged, or wrapped
+            if (!run.reqs.empty() && run.pairs + q->q > sv->opts.max_batch_pairs) break;
+            run.reqs.push_back(q);
+            run.pairs += q->q;
+        }
+        rp.nlaunched += run.reqs.size();
+    }
+    rp.leftover = rp.nlaunched < rp.live.size() && rp.live[rp.nlaunched]->staged.load(std::memory_order_acquire);
+    rp.lock.unlock();
+    return run;
+}
+
 void worker_loop(pll_server *sv) {
     cudaSetDevice(sv->device);
-    // after work the dispatcher polls for SPIN_US before it sleeps on the
-    // condition variable: a thread woken from sleep adds tens of microseconds
+    // after work the dispatcher polls for SPIN_US before it sleeps: a thread
+    // woken from sleep adds tens of microseconds
     constexpr int SPIN_US = 1000;
     Clock::time_point last_work = Clock::now();
-    uint64_t seen_seq = ~0ull;  // staged_seq at the last look at the ring
-    bool leftover = false;
     for (;;) {
         // 1. retire finished runs, oldest first
         while (!sv->inflight.empty()) {
@@ -215,68 +278,69 @@ void worker_loop(pll_server *sv) {
             sv->inflight.pop_front();
             last_work = Clock::now();
         }
-        // 2. with a free stream slot, launch the staged requests as one run;
-        // the ring is looked at only when a run could be launched (a slot is
-        // free and requests were staged since the last look, or some were left
-        // over) or when nothing is in flight (to sleep or to stop)
-        int slot = -1;
-        for (size_t i = 0; i < sv->slots.size(); ++i)
-            if (!sv->slots[i].busy) { slot = (int)i; break; }
-        Run run;
-        const uint64_t seq = sv->staged_seq.load(std::memory_order_seq_cst);
-        const bool idle = sv->inflight.empty();
-        if (idle || (slot >= 0 && (seq != seen_seq || leftover))) {
-            seen_seq = seq;
-            bool empty = false, ready = false;
-            sv->ring.lock();
-            auto first_staged = [sv] {
-                return sv->nlaunched < sv->live.size() &&
-                       sv->live[sv->nlaunched]->staged.load(std::memory_order_acquire);
-            };
-            ready = first_staged();
-            empty = sv->live.empty();
-            if (slot >= 0 && ready) {
-                run.off = sv->live[sv->nlaunched]->off;
-                for (size_t i = sv->nlaunched; i < sv->live.size(); ++i) {
-                    Request *q = sv->live[i];
-                    if (!q->staged.load(std::memory_order_acquire) || q->off != run.off + run.pairs)
-                        break;  // not staged, or wrapped
-                    if (!run.reqs.empty() && run.pairs + q->q > sv->opts.max_batch_pairs) break;
-                    run.reqs.push_back(q);
-                    run.pairs += q->q;
-                }
-                sv->nlaunched += run.reqs.size();
-                run.slot = slot;
-                sv->st.batches++;
-                sv->st.max_batch_pairs = std::max(sv->st.max_batch_pairs, run.pairs);
-            }
-            leftover = first_staged();  // staged requests the run did not take (size, wrap)
-            sv->ring.unlock();
-            if (idle && !ready) {
-                if (sv->stop.load(std::memory_order_seq_cst) && empty) return;
-                if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US))
-                    sv->work.wait_until(
-                        [&] {
-                            return sv->stop.load(std::memory_order_seq_cst) ||
-                                   sv->staged_seq.load(std::memory_order_seq_cst) != seq;
-                        },
-                        Clock::now() + std::chrono::milliseconds(2));
-                continue;
-            }
-        }
-        if (run.slot >= 0) {
-            sv->slots[run.slot].busy = true;
+        // 2. while a stream slot is free, launch the staged requests of the
+        // parts in turn, one run each; a part is looked at only when requests
+        // were staged there since the last look, or some were left over
+        bool launched = false;
+        for (uint32_t k = 0; k < sv->nparts; ++k) {
+            int slot = -1;
+            for (size_t i = 0; i < sv->slots.size(); ++i)
+                if (!sv->slots[i].busy) { slot = (int)i; break; }
+            if (slot < 0) break;
+            const uint32_t p = sv->next_part;
+            sv->next_part = (p + 1) % sv->nparts;
+            RingPart &rp = sv->parts[p];
+            const uint64_t seq = rp.staged_seq.load(std::memory_order_seq_cst);
+            if (seq == rp.seen_seq && !rp.leftover) continue;
+            rp.seen_seq = seq;
+            Run run = take_run(sv, rp);
+            if (run.reqs.empty()) continue;
+            run.slot = slot;
+            run.part = (int)p;
+            sv->stats_lock.lock();
+            sv->st.batches++;
+            sv->st.max_batch_pairs = std::max(sv->st.max_batch_pairs, run.pairs);
+            sv->stats_lock.unlock();
+            sv->slots[slot].busy = true;
             const int s = launch_run(sv, run);
             if (s != PLL_OK) {
                 // nothing of the run is in flight once the stream drains; it
                 // retires behind the runs launched before it (requests leave
                 // the ring in order)
-                cudaStreamSynchronize(sv->slots[run.slot].stream);
+                cudaStreamSynchronize(sv->slots[slot].stream);
                 sv->fatal = s;
                 run.fail = s;
             }
             sv->inflight.push_back(std::move(run));
             last_work = Clock::now();
+            launched = true;
+        }
+        if (launched || !sv->inflight.empty()) {
+            if (!launched) std::this_thread::yield();
+            continue;
+        }
+        // 3. nothing in flight and nothing launched: stop, or sleep a while.
+        // The staged count is read before the parts are looked at, so a
+        // request staged after the look changes it and ends the sleep.
+        const uint64_t seen = sv->staged_sum();
+        bool empty = true, ready = false;
+        for (uint32_t p = 0; p < sv->nparts; ++p) {
+            RingPart &rp = sv->parts[p];
+            rp.lock.lock();
+            empty = empty && rp.live.empty();
+            ready = ready || rp.leftover ||
+                    (rp.nlaunched < rp.live.size() && rp.live[rp.nlaunched]->staged.load(std::memory_order_acquire));
+            rp.lock.unlock();
+        }
+        if (ready) {
+            for (uint32_t p = 0; p < sv->nparts; ++p) sv->parts[p].leftover = true;  // look again
+            continue;
+        }
+        if (sv->stop.load(std::memory_order_seq_cst) && empty) return;
+        if (Clock::now() - last_work > std::chrono::microseconds(SPIN_US)) {
+            sv->work.wait_until(
+                [&] { return sv->stop.load(std::memory_order_seq_cst) || sv->staged_sum() != seen; },
+                Clock::now() + std::chrono::milliseconds(2));
         } else {
             std::this_thread::yield();
         }
@@ -290,12 +354,15 @@ void destroy(pll_server *sv) {
         if (sl.done) cudaEventDestroy(sl.done);
     }
     if (sv->h_pairs) cudaFreeHost(sv->h_pairs);
-    // a request is in `live` until its run retires, and in its shard from
-    // staging until it is waited for: completed ones are only in a shard
+    // a request is in its part's `live` until its run retires, and in its
+    // shard from staging until it is waited for: completed ones are only in a
+    // shard
     for (Shard &sh : sv->shards)
         for (auto &kv : sh.map)
             if (kv.second->done.load()) delete kv.second;
-    for (Request *r : sv->live) delete r;
+    if (sv->parts)
+        for (uint32_t p = 0; p < sv->nparts; ++p)
+            for (Request *r : sv->parts[p].live) delete r;
     delete sv;
 }
 
@@ -320,7 +387,15 @@ PLL_API int pll_server_start(const pll_index *idx, const pll_server_opts *opts, 
     sv->opts = o;
     sv->device = idx->device;
     sv->P = P;
-    sv->max_request = std::min<uint64_t>(o.max_batch_pairs, P);
+    // parts only where each still holds two of the largest runs
+    sv->nparts = (uint32_t)std::min<uint64_t>(MAX_PARTS, std::max<uint64_t>(1, P / (2 * o.max_batch_pairs)));
+    sv->parts.reset(new (std::nothrow) RingPart[sv->nparts]);
+    if (!sv->parts) { delete sv; return PLL_E_NOMEM; }
+    for (uint32_t p = 0; p < sv->nparts; ++p) {
+        sv->parts[p].base = P / sv->nparts * p;
+        sv->parts[p].cap = p + 1 < sv->nparts ? P / sv->nparts : P - P / sv->nparts * p;
+    }
+    sv->max_request = std::min<uint64_t>(o.max_batch_pairs, P / sv->nparts);
     sv->st.pool_bytes = 9 * P;
     sv->st.max_request_pairs = sv->max_request;
     cudaError_t e = cudaSetDevice(sv->device);
@@ -362,26 +437,29 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
     r->q = q;
     r->out = out;
     r->t_submit = Clock::now();
-    // admission: q contiguous ring slots, else sleep until a run retires
+    const uint32_t part = client_part(sv->nparts);
+    RingPart &rp = sv->parts[part];
+    // admission: q contiguous slots of this thread's part, else sleep until a
+    // run of the part retires
+    auto try_admit = [&] {
+        uint64_t off = 0;
+        rp.lock.lock();
+        const bool ok = ring_alloc(rp, q, &off);
+        if (ok) {
+            r->off = off;
+            r->ticket = part + 1 + rp.next_seq++ * sv->nparts;
+            rp.live.push_back(r);
+            rp.max_inflight_bytes = std::max(rp.max_inflight_bytes, 9 * ring_used(rp));
+            rp.requests++;
+            rp.pairs += q;
+        }
+        rp.lock.unlock();
+        return ok;
+    };
     for (bool admitted = false; !admitted;) {
         if (sv->stop.load(std::memory_order_seq_cst)) { delete r; return PLL_E_INVAL; }
-        auto try_admit = [&] {
-            uint64_t off = 0;
-            sv->ring.lock();
-            const bool ok = ring_alloc(sv->live, sv->P, q, &off);
-            if (ok) {
-                r->off = off;
-                r->ticket = sv->next_ticket++;
-                sv->live.push_back(r);
-                sv->st.max_inflight_bytes = std::max(sv->st.max_inflight_bytes, 9 * ring_used(sv->live, sv->P));
-                sv->st.requests++;
-                sv->st.pairs += q;
-            }
-            sv->ring.unlock();
-            return ok;
-        };
         if (try_admit()) break;
-        sv->space.wait_until(
+        rp.space.wait_until(
             [&] { return sv->stop.load(std::memory_order_seq_cst) || (admitted = try_admit()); },
             Clock::now() + std::chrono::milliseconds(10));
     }
@@ -409,7 +487,7 @@ PLL_API int pll_server_submit(pll_server *sv, const uint32_t *src, const uint32_
     }
     sv->pack_ns.fetch_add((unsigned long long)(us_between(t0, Clock::now()) * 1e3), std::memory_order_relaxed);
     r->staged.store(true, std::memory_order_release);  // pairs and ticket before the flag
-    sv->staged_seq.fetch_add(1, std::memory_order_seq_cst);
+    rp.staged_seq.fetch_add(1, std::memory_order_seq_cst);
     sv->work.wake();
     if (bad) return PLL_E_INVAL;
     *ticket = tk;
@@ -533,9 +611,18 @@ PLL_API int pll_server_replay(pll_server *sv, const uint32_t *src, const uint32_
 
 PLL_API int pll_server_get_stats(pll_server *sv, pll_server_stats *out) {
     if (!sv || !out) return PLL_E_INVAL;
-    sv->ring.lock();
+    sv->stats_lock.lock();
     *out = sv->st;
-    sv->ring.unlock();
+    sv->stats_lock.unlock();
+    out->requests = out->pairs = out->max_inflight_bytes = 0;
+    for (uint32_t p = 0; p < sv->nparts; ++p) {  // the parts' peaks, summed
+        RingPart &rp = sv->parts[p];
+        rp.lock.lock();
+        out->requests += rp.requests;
+        out->pairs += rp.pairs;
+        out->max_inflight_bytes += rp.max_inflight_bytes;
+        rp.lock.unlock();
+    }
     out->pack_us = sv->pack_ns.load(std::memory_order_relaxed) / 1e3;
     return PLL_OK;
 }
@@ -544,7 +631,7 @@ PLL_API int pll_server_stop(pll_server *sv) {
     if (!sv) return PLL_OK;
     sv->stop.store(true, std::memory_order_seq_cst);
     sv->work.wake();
-    sv->space.wake();
+    for (uint32_t p = 0; p < sv->nparts; ++p) sv->parts[p].space.wake();
     if (sv->worker.joinable()) sv->worker.join();
     const int s = sv->fatal;
     destroy(sv);
