@@ -324,12 +324,16 @@ PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *
  * waited for. The server holds a ring of P = pool_bytes / 9 pair slots (8
  * bytes per pair, 1 per result) in pinned, mapped host memory that the GPU
  * reads and writes directly (over NVLink-C2C on a GB300; no copies):
- *   - admission by memory: a request is admitted when q contiguous slots are
- *     free; until then pll_server_submit blocks. Its slots are held until its
+ *   - admission by memory: a ring of at least 4 * max_batch_pairs slots is
+ *     cut into up to four parts (each at least 2 * max_batch_pairs), each
+ *     with its own lock; a client thread always uses the same part. A
+ *     request is admitted when q contiguous slots of its part are free;
+ *     until then pll_server_submit blocks. Its slots are held until its
  *     results are back, so at most P pairs are queued or in flight;
  *   - continuous batching: one dispatcher thread launches, whenever one of
- *     `streams` stream slots is free, every admitted request not yet launched
- *     (arrival order, up to max_batch_pairs pairs) as one query launch that
+ *     `streams` stream slots is free, the admitted requests not yet launched
+ *     at the head of a part (arrival order, up to max_batch_pairs pairs; the
+ *     parts in turn) as one query launch that
  *     reads the pairs from the ring and writes the results into it; requests
  *     that arrive while others are on the
  *     GPU form the next launch, and launches on different stream slots
@@ -346,8 +350,9 @@ PLL_API int pll_bp_labels_noalloc(const uint32_t *rank_offsets, const uint32_t *
  *                    or reserved != 0; PLL_E_NOMEM if the ring cannot be
  *                    allocated.
  * pll_server_submit  admits and stages a request and returns its ticket.
- *                    PLL_E_RANGE if q exceeds min(max_batch_pairs, P) (stats
- *                    field max_request_pairs), PLL_E_INVAL if an id is >= n
+ *                    PLL_E_RANGE if q exceeds min(max_batch_pairs, P /
+ *                    parts) (stats field max_request_pairs), PLL_E_INVAL if
+ *                    an id is >= n
  *                    (nothing is queued for the caller then).
  * pll_server_wait    waits for a ticket (timeout_us < 0: no limit; on
  *                    PLL_E_TIMEOUT the ticket stays valid), writes its latency
@@ -377,7 +382,8 @@ typedef struct pll_server_opts {
 typedef struct pll_server_stats {
     uint64_t requests, pairs, batches;  /* submitted requests and pairs; launches */
     uint64_t max_batch_pairs;           /* largest batch launched */
-    uint64_t max_inflight_bytes;        /* peak pool bytes held by batches */
+    uint64_t max_inflight_bytes;        /* peak pool bytes held (the ring
+                                           parts' peaks, summed) */
     uint64_t pool_bytes;                /* the pool's size */
     uint64_t max_request_pairs;         /* largest request accepted */
     double pack_us;                     /* client time staging pairs at submit */
