@@ -26,9 +26,11 @@
  *     before they return.
  *   - Every function returns a pll_status; no C++ exception crosses the ABI.
  *     On failure no output is valid and nothing is leaked. Apart from the
- *     scratch array of pll_bp_labels_noalloc, the library holds no global
- *     mutable state between calls; an index is immutable after pll_build, so
- *     queries on one index may run concurrently on different streams.
+ *     scratch array of pll_bp_labels_noalloc and the scratch memory pool of
+ *     each CUDA context (freed temporaries kept mapped for later calls; see
+ *     pll_release_cached), the library holds no global mutable state between
+ *     calls; an index is immutable after pll_build, so queries on one index
+ *     may run concurrently on different streams.
  */
 #ifndef PLL_H
 #define PLL_H
@@ -239,11 +241,11 @@ PLL_API int pll_query_errors(const pll_index *idx, void *stream, uint64_t *count
 /* pll_query_host -- as pll_query with HOST src, dst and out; the copies to
  * and from the device happen inside the call.
  *
- * Staging (pll_build_host, pll_query_host): the device copies live in a
- * stream-ordered memory pool of this library, one per CUDA context, which
- * keeps up to 1 GiB of freed staging memory mapped between calls (remapping
- * ~100 MB on every call cost milliseconds). A staging allocation that fails
- * returns PLL_E_NOMEM. */
+ * Staging (pll_build_host, pll_query_host): the device copies are
+ * stream-ordered allocations from the library's scratch pool (see
+ * pll_release_cached), so a repeated call does not map its ~100 MB of
+ * staging afresh (that cost milliseconds per call). A staging allocation
+ * that fails returns PLL_E_NOMEM. */
 PLL_API int pll_query_host(const pll_index *idx, const uint32_t *src, const uint32_t *dst,
                            uint64_t q, uint8_t *out, void *stream);
 
